@@ -1,0 +1,135 @@
+"""K u, g(u) and the PHISPLIT time steppers, FP64 (oracle; test infrastructure).
+
+Tensor formulations of Section 3.2 with tensors in the (n_d, ..., n_1) layout:
+
+* K u without assembling K:  sum_mu U x_mu A_mu                 (Section 3.2)
+* exponential Euler (eq. (19)):
+      U+ = U + tau * (K U + G(U)) x_1 phi_1(tau A_1) ... x_d phi_1(tau A_d)
+* ETD2RK (eq. (20), read with tau multiplying both K U and G, as the vector form
+  eq. (12) requires, and with the (2!)^(d-1) factor of P_2^(2) from Theorem 1):
+      U2 = U  + tau * P_1^(2)(K U + G(U))
+      U+ = U2 + tau * P_2^(2)(G(U2) - G(U))
+  where P_l^(2)(V) = ((l!)^(d-1) V) x_1 phi_l(tau A_1) ... x_d phi_l(tau A_d).
+* Lawson-Euler (eq. (17)):  U+ = (U + tau G(U)) x_mu e^{tau A_mu}
+* Lawson2b (eq. (18)):
+      U2 = (U + tau G(U)) x_mu e^{tau A_mu}
+      U+ = (U + tau/2 G(U)) x_mu e^{tau A_mu} + tau/2 G(U2)
+
+g may depend on t only through the manufactured forcing of the paper's ADR test
+(Section 4.2): g(t, u) = 1/(1 + u^2) + e^t a - 1/(1 + e^{2t} b^2), with the
+arrays a, b supplied by the caller.  Stage times follow eq. (9)-(12): G(t_n, U_n)
+and, for the second stages, G(t_{n+1}, U_n2).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from .phi import phi_matrices
+from .tucker import mode_product, phisplit_apply
+
+G_NONE, G_CUBIC, G_RICCATI, G_ADR_MANUFACTURED = 0, 1, 2, 3
+EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B = 0, 1, 2, 3
+
+
+@dataclasses.dataclass
+class OracleProblem:
+    """Everything one integration needs; built by the caller from plain arrays."""
+    A: List[np.ndarray]
+    tau: float
+    g_kind: int = G_NONE
+    cubic: Sequence[float] = (0.0, 0.0, 0.0, 0.0)
+    B: Optional[np.ndarray] = None
+    C: Optional[np.ndarray] = None
+    psi_a: Optional[np.ndarray] = None
+    psi_b: Optional[np.ndarray] = None
+    phis: Optional[List[List[np.ndarray]]] = None   # phis[mu-1][l] = phi_l(tau A_mu)
+
+    def ensure_phis(self, lmax: int = 2) -> None:
+        if self.phis is None or len(self.phis[0]) <= lmax:
+            self.phis = [phi_matrices(self.tau * A, lmax) for A in self.A]
+
+    def phi_list(self, ell: int) -> List[np.ndarray]:
+        return [p[ell] for p in self.phis]
+
+    @classmethod
+    def from_problem(cls, p, lmax: int = 2) -> "OracleProblem":
+        op = cls(A=[np.asarray(a, dtype=np.float64) for a in p.A], tau=float(p.tau),
+                 g_kind=p.g_kind, cubic=tuple(p.cubic), B=p.B, C=p.C,
+                 psi_a=getattr(p, "psi_a", None), psi_b=getattr(p, "psi_b", None))
+        op.ensure_phis(lmax)
+        return op
+
+
+def kron_apply(U: np.ndarray, A: Sequence[np.ndarray]) -> np.ndarray:
+    """K u in tensor form: sum_mu U x_mu A_mu (Section 3.2)."""
+    out = np.zeros_like(U, dtype=np.float64)
+    for mu, Amu in enumerate(A, start=1):
+        out += mode_product(U, Amu, mu)
+    return out
+
+
+def g_eval(op: OracleProblem, U: np.ndarray, t: float = 0.0) -> np.ndarray:
+    """G(t, U): zero, a pointwise cubic, the Riccati term C + U B U (eq. (2)),
+    or the manufactured ADR nonlinearity of Section 4.2."""
+    if op.g_kind == G_NONE:
+        return np.zeros_like(U)
+    if op.g_kind == G_CUBIC:
+        c0, c1, c2, c3 = op.cubic
+        return c0 + c1 * U + c2 * U * U + c3 * U * U * U
+    if op.g_kind == G_RICCATI:
+        # Stored arrays are (n_2, n_1) = transposes of the n_1 x n_2 matrices.
+        Um = U.T
+        Cm = op.C.T
+        return np.ascontiguousarray((Cm + Um @ op.B @ Um).T)
+    if op.g_kind == G_ADR_MANUFACTURED:
+        et = np.exp(t)
+        return (1.0 / (1.0 + U * U) + et * op.psi_a
+                - 1.0 / (1.0 + et * et * op.psi_b * op.psi_b))
+    raise ValueError(f"unknown g kind {op.g_kind}")
+
+
+def step(op: OracleProblem, U: np.ndarray, scheme: int, t: float = 0.0) -> np.ndarray:
+    """One step of size op.tau from (t, U) (Section 3.2 tensor formulations)."""
+    tau = op.tau
+    if scheme == EXPEULER:
+        W = kron_apply(U, op.A) + g_eval(op, U, t)
+        return U + tau * phisplit_apply(W, op.phi_list(1), 1)
+    if scheme == ETD2RK:
+        Gn = g_eval(op, U, t)
+        W1 = kron_apply(U, op.A) + Gn
+        U2 = U + tau * phisplit_apply(W1, op.phi_list(1), 1)
+        W2 = g_eval(op, U2, t + tau) - Gn
+        return U2 + tau * phisplit_apply(W2, op.phi_list(2), 2)
+    if scheme == LAWSON_EULER:
+        return phisplit_apply(U + tau * g_eval(op, U, t), op.phi_list(0), 0)
+    if scheme == LAWSON2B:
+        Gn = g_eval(op, U, t)
+        U2 = phisplit_apply(U + tau * Gn, op.phi_list(0), 0)
+        return (phisplit_apply(U + 0.5 * tau * Gn, op.phi_list(0), 0)
+                + 0.5 * tau * g_eval(op, U2, t + tau))
+    raise ValueError(f"unknown scheme {scheme}")
+
+
+def integrate(op: OracleProblem, U0: np.ndarray, scheme: int, nsteps: int,
+              t0: float = 0.0) -> np.ndarray:
+    """nsteps constant-size steps from (t0, U0)."""
+    op.ensure_phis(2)
+    U = np.array(U0, dtype=np.float64, copy=True)
+    for k in range(nsteps):
+        U = step(op, U, scheme, t0 + k * op.tau)
+    return U
+
+
+def rel_err_inf(x: np.ndarray, ref: np.ndarray) -> float:
+    """||x - ref||_inf / ||ref||_inf (the ADR convention of Section 4.2)."""
+    den = np.max(np.abs(ref))
+    return float(np.max(np.abs(x - ref)) / (den if den > 0 else 1.0))
+
+
+def rel_err_fro(x: np.ndarray, ref: np.ndarray) -> float:
+    """||x - ref||_F / ||ref||_F (the Riccati convention of Section 4.1)."""
+    den = np.linalg.norm(ref.ravel())
+    return float(np.linalg.norm((x - ref).ravel()) / (den if den > 0 else 1.0))

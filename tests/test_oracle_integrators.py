@@ -1,0 +1,132 @@
+"""Pins of the oracle's K u, g and time steppers (Section 2, Section 3.2).
+
+Against: the assembled Kronecker sum (eq. (1b)), the Riccati vec form (eq. (3)),
+exactness statements of Section 2 (exponential Euler exact for linear
+constant-coefficient problems, Lawson-Euler exact for linear homogeneous ones),
+and observed convergence orders against an independent high-accuracy ODE
+solve (scipy.integrate.solve_ivp), as in the paper's order tables.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+import oracle.integrators as oi
+from oracle.integrators import OracleProblem, kron_apply, g_eval, integrate
+from paper_2304_02327_gb300 import workloads as wl
+from tests.test_oracle_tucker import kron_sum, vec
+
+
+def test_kron_apply_equals_assembled_K():
+    ns = (4, 3, 5)
+    As = [wl.fd_matrix(n, 0.4, -0.9) + 0.2 * wl.random_dense(n, 10 + n) for n in ns]
+    U = wl.random_tensor(tuple(reversed(ns)), 3)
+    assert np.abs(vec(kron_apply(U, As)) - kron_sum(As) @ vec(U)).max() < 1e-12
+
+
+def test_riccati_kronecker_form_eq3():
+    n = 6
+    p = wl.riccati_2d(n, seed=2)
+    op = OracleProblem.from_problem(p, lmax=1)
+    Um = np.random.default_rng(0).standard_normal((n, n))
+    Ust = np.ascontiguousarray(Um.T)                         # stored (n_2, n_1)
+    KU = kron_apply(Ust, p.A).T
+    assert np.abs(KU - (p.A[0] @ Um + Um @ p.A[1].T)).max() < 1e-9
+    # eq. (3): ((I (x) A1) + (A2 (x) I)) vec(U) + vec(C + U B U), vec stacks columns
+    Kmat = np.kron(np.eye(n), p.A[0]) + np.kron(p.A[1], np.eye(n))
+    rhs = Kmat @ Um.reshape(-1, order="F") + (p.C.T + Um @ p.B @ Um).reshape(-1, order="F")
+    got = vec(kron_apply(Ust, p.A) + g_eval(op, Ust))
+    assert np.abs(got - rhs).max() < 1e-9 * np.abs(rhs).max()
+
+
+def test_expeuler_d1_linear_is_exact():
+    """d = 1 (no splitting): exponential Euler is exact for u' = A u + c (Section 2)."""
+    n, tau = 12, 0.03
+    A = wl.fd_matrix(n, 0.2, 0.5)
+    u = wl.random_tensor((n,), 1)
+    c = 0.3
+    op = OracleProblem(A=[A], tau=tau, g_kind=oi.G_CUBIC, cubic=(c, 0, 0, 0))
+    got = integrate(op, u, oi.EXPEULER, 3)
+    Z = np.zeros((n + 1, n + 1))
+    Z[:n, :n] = A
+    Z[:n, n] = c
+    ref = (scipy.linalg.expm(3 * tau * Z) @ np.append(u, 1.0))[:n]
+    assert np.abs(got - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("scheme", [oi.LAWSON_EULER, oi.LAWSON2B])
+def test_lawson_linear_homogeneous_is_exact(scheme):
+    """g = 0: Lawson schemes give e^{tau K} u per step, no splitting error (Section 3.2)."""
+    ns = (4, 5)
+    As = [wl.fd_matrix(n, 0.3, 0.4) for n in ns]
+    U = wl.random_tensor(tuple(reversed(ns)), 2)
+    op = OracleProblem(A=As, tau=0.05)
+    got = integrate(op, U, scheme, 4)
+    ref = scipy.linalg.expm(0.2 * kron_sum(As)) @ vec(U)
+    assert np.abs(vec(got) - ref).max() < 1e-12
+
+
+def small_adr(ns=(5, 6, 4), eps=0.05, beta=0.5, seed=8):
+    As = [wl.fd_matrix(n, eps, beta) for n in ns]
+    U0 = 0.5 + 0.3 * wl.random_tensor(tuple(reversed(ns)), seed)
+    return As, U0
+
+
+def reference_solution(As, U0, cubic, T):
+    K = kron_sum(As)
+    c0, c1, c2, c3 = cubic
+    f = lambda t, u: K @ u + c0 + c1 * u + c2 * u * u + c3 * u * u * u
+    sol = scipy.integrate.solve_ivp(f, (0, T), vec(U0), method="DOP853",
+                                    rtol=1e-13, atol=1e-14)
+    return sol.y[:, -1]
+
+
+def observed_orders(scheme, cubic=(0.0, -0.5, 1.5, -1.0), T=0.5, steps=(8, 16, 32, 64)):
+    As, U0 = small_adr()
+    ref = reference_solution(As, U0, cubic, T)
+    errs = []
+    for m in steps:
+        op = OracleProblem(A=As, tau=T / m, g_kind=oi.G_CUBIC, cubic=cubic)
+        errs.append(np.abs(vec(integrate(op, U0, scheme, m)) - ref).max())
+    return [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+
+
+@pytest.mark.parametrize("scheme,order", [(oi.EXPEULER, 1), (oi.ETD2RK, 2),
+                                          (oi.LAWSON_EULER, 1), (oi.LAWSON2B, 2)])
+def test_observed_order(scheme, order):
+    """Global order on a step sweep: 1 for (Lawson-/exponential) Euler, 2 for
+    ETD2RK and Lawson2b, as in the paper's order tables (Section 4)."""
+    o = observed_orders(scheme)
+    assert abs(o[-1] - order) < 0.15, o
+
+
+def test_planted_missing_factor_breaks_etd2rk_order(monkeypatch):
+    """A planted mistake in the oracle -- dropping the (2!)^(d-1) factor of the
+    phi_2 stage (eq. (20) as printed) -- must fail the order pin."""
+    real = oi.phisplit_apply
+
+    def wrong(V, phis, ell):
+        out = real(V, phis, ell)
+        return out / 2 ** (V.ndim - 1) if ell == 2 else out
+
+    monkeypatch.setattr(oi, "phisplit_apply", wrong)
+    o = observed_orders(oi.ETD2RK)
+    assert abs(o[-1] - 2) > 0.5, o
+
+
+def test_planted_missing_tau_breaks_consistency(monkeypatch):
+    """Planting the other reading of eq. (20) (tau on G only) gives an
+    inconsistent scheme: the error does not decrease with the step."""
+    def wrong_step(op, U, scheme, t=0.0):
+        Gn = g_eval(op, U, t)
+        W1 = kron_apply(U, op.A) / op.tau + Gn
+        U2 = U + op.tau * oi.phisplit_apply(W1, op.phi_list(1), 1)
+        return U2 + op.tau * oi.phisplit_apply(g_eval(op, U2, t + op.tau) - Gn, op.phi_list(2), 2)
+
+    monkeypatch.setattr(oi, "step", wrong_step)
+    with np.errstate(all="ignore"):
+        o = observed_orders(oi.ETD2RK, steps=(8, 16, 32))
+    # either it diverges (nan/inf) or the error stops decreasing
+    assert not (abs(o[-1] - 2) < 0.5), o
