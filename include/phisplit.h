@@ -1,0 +1,205 @@
+/*
+ * phisplit.h -- C ABI of the GB300 (sm_103a) direction-split phi-function library.
+ *
+ * The library computes the PHISPLIT approximation of Caliari & Cassini,
+ * "Direction splitting of phi-functions in exponential integrators for
+ * d-dimensional problems in Kronecker form" (arXiv 2304.02327):
+ *
+ *   phi_l(tau K) v  ~  vec( ((l!)^(d-1) V) x_1 phi_l(tau A_1) x_2 ... x_d phi_l(tau A_d) )
+ *
+ * for a Kronecker sum K = A_d (+) ... (+) A_1 (Section 1, eq. (1b); Section 3,
+ * Theorem 1 / eq. (14) and the definition of P_l^(2) after it), and the
+ * exponential integrators built on it (Section 3.2, eq. (17)-(20)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Layout.  An order-d tensor of sizes n_1 x ... x n_d is a contiguous device
+ *   array of N = n_1 * ... * n_d doubles, index i_1 fastest (the column-stacking
+ *   vec of Section 1).  Small matrices are n x n, column-major (entry (i, j) at
+ *   i + n*j).  A_1 acts on i_1.
+ * - Pointers.  Every array argument is a DEVICE pointer unless its comment says
+ *   host.  The caller owns every buffer it passes; the plan owns the phi
+ *   matrices it forms and frees them in phi_plan_destroy.
+ * - Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  All calls are stream-ordered and return without synchronising,
+ *   except phi_plan_create, phi_plan_status and the *_info queries, which say so.
+ * - Errors.  Every call returns MM_OK (0) or a negative MM_ERR_* code and leaves
+ *   its outputs unspecified on error.  Argument and shape errors are detected on
+ *   the host before any launch.  Device-side conditions (a non-finite value
+ *   written by an integrator step, a bounded wait that ran out) are OR-ed into a
+ *   per-plan status word that phi_plan_status reads.
+ * - Precision.  MM_FP64: every product and sum in double (the plain form).
+ *   MM_TF32X3: the mu-mode products run on tcgen05 tensor cores with operands
+ *   split x = hi + lo into TF32 parts and hi*hi + hi*lo + lo*hi accumulated in
+ *   FP32; phi matrices, K u + g and the state update stay FP64.
+ */
+#ifndef PHISPLIT_H
+#define PHISPLIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MM_API __attribute__((visibility("default")))
+#else
+#define MM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define MM_OK               0
+#define MM_ERR_ARG         -1   /* null pointer, bad enum, bad scalar          */
+#define MM_ERR_SHAPE       -2   /* sizes out of range or inconsistent          */
+#define MM_ERR_UNSUPPORTED -3   /* valid request this build does not implement */
+#define MM_ERR_CUDA        -4   /* a CUDA runtime call failed                  */
+#define MM_ERR_TIMEOUT     -5   /* a bounded device wait ran out               */
+#define MM_ERR_NONFINITE   -6   /* a step produced inf/nan                     */
+#define MM_ERR_NOMEM       -7   /* device allocation failed (plan creation)    */
+#define MM_ERR_WORKSPACE   -8   /* workspace missing or too small              */
+
+/* Device status-word bits (phi_plan_status). */
+#define MM_STATUS_NONFINITE 1u
+#define MM_STATUS_TIMEOUT   2u
+
+/* ---- precision forms ------------------------------------------------- */
+#define MM_FP64    0
+#define MM_TF32X3  1
+
+/* ---- time-stepping schemes (Section 2 and Section 3.2) ----------------- */
+#define MM_EXPEULER     0   /* eq. (11) / tensor form eq. (19)               */
+#define MM_ETD2RK       1   /* eq. (12) / tensor form eq. (20)               */
+#define MM_LAWSON_EULER 2   /* eq. (9)  / tensor form eq. (17)               */
+#define MM_LAWSON2B     3   /* eq. (10) / tensor form eq. (18)               */
+
+/* ---- nonlinearity g(t, u) (eq. (1a)) ----------------------------------- */
+#define MM_G_NONE            0  /* g = 0                                         */
+#define MM_G_CUBIC           1  /* g = c0 + c1 u + c2 u^2 + c3 u^3, pointwise    */
+#define MM_G_RICCATI         2  /* G(U) = C + U B U, d = 2 (eq. (2)-(3))         */
+#define MM_G_ADR_MANUFACTURED 3 /* g = 1/(1+u^2) + e^t a - 1/(1 + e^{2t} b^2),   */
+                                /* the paper's ADR test (Section 4.2, eq. (25))  */
+
+typedef struct mm_nonlin {
+    int kind;              /* MM_G_*                                              */
+    double c[4];           /* MM_G_CUBIC coefficients c0..c3                      */
+    const double* B;       /* MM_G_RICCATI: n_2 x n_1, column-major (device)      */
+    const double* C;       /* MM_G_RICCATI: n_1 x n_2, column-major (device)      */
+    const double* psi_a;   /* MM_G_ADR_MANUFACTURED: N doubles, tensor layout     */
+    const double* psi_b;   /* MM_G_ADR_MANUFACTURED: N doubles, tensor layout     */
+} mm_nonlin;
+
+/* Opaque, immutable after creation (apart from its status word and its cache of
+ * captured CUDA graphs).  One plan may be used from one host thread at a time. */
+typedef struct mm_plan_s* mm_plan;
+
+/*
+ * phi_plan_create -- form phi_l(tau A_mu), l = 0..ell_max, for every direction
+ * (Section 3.1: scaling so that ||tau A / 2^s||_1 <= 1/2, a truncated Taylor
+ * series of phi_ell_max at the scaled matrix, phi_{l-1}(X) = X phi_l(X) + I/(l-1)!,
+ * then s applications of the squaring recurrence eq. (16)), all in FP64 on the
+ * GPU.  Directions whose A_mu are bitwise equal share one set of phi matrices.
+ * If every A_mu is tridiagonal, K u is evaluated later as a 3-point stencil;
+ * otherwise as dense mu-mode products.
+ *
+ *   out     host pointer receiving the plan handle.
+ *   d       number of directions, 1 <= d <= 8.
+ *   n       host array of d sizes, 1 <= n_mu <= 8192, N = prod n_mu < 2^40.
+ *   A       host array of d device pointers; A[mu] is n_mu x n_mu column-major.
+ *           Read during the call only.
+ *   tau     time step (finite).  tau = 0 is allowed (phi_l = I / l!).
+ *   ell_max highest phi index needed, 0..3 (ETD2RK needs 2).
+ *   prec    MM_FP64 or MM_TF32X3.
+ *   stream  ordering stream for the set-up kernels.
+ * Synchronises `stream` (it reads norms and band widths back).  Allocates the
+ * plan's device memory with cudaMalloc.  Errors: MM_ERR_ARG, MM_ERR_SHAPE,
+ * MM_ERR_NOMEM, MM_ERR_CUDA; *out is NULL on error.
+ */
+MM_API int phi_plan_create(mm_plan* out, int d, const int64_t* n, const double* const* A,
+                    double tau, int ell_max, int prec, void* stream);
+
+/* Frees the plan and everything it owns (synchronises the device).  NULL is OK. */
+MM_API int phi_plan_destroy(mm_plan p);
+
+/*
+ * phi_plan_info -- host query of a plan.  Any output pointer may be NULL.
+ *   d (1), n (d entries), ell_max (1), prec (1), squarings (d entries: the s used
+ *   for direction mu), tridiagonal (1: 1 if K u runs as a stencil).
+ */
+MM_API int phi_plan_info(mm_plan p, int* d, int64_t* n, int* ell_max, int* prec,
+                  int* squarings, int* tridiagonal);
+
+/*
+ * phi_plan_get_phi -- copy phi_ell(tau A_mu) (mu = 1..d, FP64, n_mu x n_mu,
+ * column-major) into the device buffer dst.  Stream-ordered.
+ * Errors: MM_ERR_ARG (ell > ell_max, mu out of range, dst NULL), MM_ERR_CUDA.
+ */
+MM_API int phi_plan_get_phi(mm_plan p, int ell, int mu, double* dst, void* stream);
+
+/*
+ * phi_plan_status -- synchronises `stream`, returns the OR of MM_STATUS_* bits
+ * raised on the device since the last reset (>= 0), or a negative MM_ERR_*.
+ * reset != 0 clears the word afterwards.
+ */
+MM_API int phi_plan_status(mm_plan p, int reset, void* stream);
+
+/* Workspace bytes mumode_phi_apply needs (N doubles when d >= 2, else 0). */
+MM_API size_t mumode_workspace_bytes(mm_plan p);
+
+/*
+ * mumode_phi_apply -- P = alpha * (ell!)^(d-1) * V x_1 phi_ell(tau A_1) ... x_d
+ * phi_ell(tau A_d), the tensor formulation P_l^(2) of Section 3 (Theorem 1);
+ * for ell = 0 this is the exact e^{tau K} v of eq. (5)-(6).
+ *
+ *   V   N doubles (input, not modified).  P: N doubles (output).  V and P must
+ *       not overlap.  ws: workspace of >= mumode_workspace_bytes(p) bytes,
+ *       8-byte aligned, overlapping neither V nor P.
+ * Errors: MM_ERR_ARG (ell > ell_max, null pointers, overlap), MM_ERR_WORKSPACE,
+ * MM_ERR_CUDA (launch failure).
+ */
+MM_API int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, double alpha,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes expint_step needs for `scheme` and nonlinearity `g`. */
+MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
+
+/*
+ * expint_step -- advance U in place by nsteps steps of size tau (the plan's)
+ * with the PHISPLIT form of `scheme` (Section 3.2):
+ *   MM_EXPEULER     U+ = U + tau P_1^(2)(K U + G(t, U))                   eq. (19)
+ *   MM_ETD2RK       U2 = U + tau P_1^(2)(K U + G(t, U))
+ *                   U+ = U2 + tau P_2^(2)(G(t + tau, U2) - G(t, U))       eq. (20)
+ *   MM_LAWSON_EULER U+ = (U + tau G(t, U)) x_mu e^{tau A_mu}              eq. (17)
+ *   MM_LAWSON2B     eq. (18)
+ * P_l^(2) carries the (l!)^(d-1) factor of Theorem 1 (so the phi_2 stage of
+ * ETD2RK is scaled by 2^(d-1)), and tau multiplies both K U and G in the first
+ * stage, as the vector forms eq. (11)-(12) require.
+ *
+ *   g       host pointer to the nonlinearity descriptor (device arrays inside).
+ *           MM_G_RICCATI requires d = 2; MM_G_ADR_MANUFACTURED requires psi_a,
+ *           psi_b of N doubles.
+ *   U       N doubles, in/out.
+ *   t0      time of the first step (used by time-dependent g only).
+ *   nsteps  >= 0.
+ *   ws      >= expint_workspace_bytes(p, scheme, g) bytes, 8-byte aligned, not
+ *           overlapping U or g's arrays.
+ * The ell_max of the plan must cover the scheme (ETD2RK: 2, exp. Euler: 1,
+ * Lawson: 0).  A non-finite value in the updated state raises
+ * MM_STATUS_NONFINITE in the plan's status word.
+ * Errors: MM_ERR_ARG, MM_ERR_UNSUPPORTED, MM_ERR_WORKSPACE, MM_ERR_CUDA.
+ */
+MM_API int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,
+                int nsteps, void* ws, size_t ws_bytes, void* stream);
+
+/* Human-readable name of a status code (static string). */
+MM_API const char* mm_status_str(int code);
+
+/* Library version, major*10000 + minor*100 + patch. */
+MM_API int mm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHISPLIT_H */

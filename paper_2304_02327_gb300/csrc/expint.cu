@@ -1,0 +1,303 @@
+// Orchestration: the PHISPLIT Tucker chain (Section 3, P_l^(2)) and the time
+// steppers of Section 3.2 (eq. (17)-(20)), as stream-ordered launches of the
+// contraction kernels (FP64: dgemm.cu, TF32x3: tf32.cu) and the prepass.
+//
+// Per step the big tensor makes d passes per Tucker.  Intermediates ping-pong
+// between two N-double buffers; the last mode's epilogue performs the
+// integrator's update in FP64 (U+ = U + tau*Y, the ETD2RK stage values and
+// g(U2) - g(U)), so no separate elementwise pass touches HBM.
+#include <math.h>
+#include <string.h>
+
+#include "plan.cuh"
+#include "stencil.cuh"
+#include "tf32.cuh"
+
+namespace mm {
+
+namespace {
+
+double factorial(int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= i;
+    return f;
+}
+
+int mode_product(mm_plan_s* p, int ell, int mu, const double* in, const Epi& e, cudaStream_t s) {
+    if (p->prec == MM_TF32X3) return tf32_mode_product(p, ell, mu, in, e, s);
+    Gemm g = mode_gemm(p->d, p->n, mu, p->phi[mu - 1][ell], in);
+    return launch_dgemm(g, e, s);
+}
+
+// Modes 1..d-1 store into outs[0..d-2]; mode d applies `last`.
+int tucker_chain(mm_plan_s* p, int ell, const double* in, double* const* outs, const Epi& last,
+                 cudaStream_t s) {
+    const double* cur = in;
+    for (int mu = 1; mu < p->d; ++mu) {
+        Epi e{};
+        e.kind = EPI_STORE;
+        e.alpha = 1.0;
+        e.C = outs[mu - 1];
+        int rc = mode_product(p, ell, mu, cur, e, s);
+        if (rc) return rc;
+        cur = outs[mu - 1];
+    }
+    return mode_product(p, ell, p->d, cur, last, s);
+}
+
+// Alternating outputs X->Y->X... starting from Y; returns the buffer free in the last mode.
+double* ping_pong(int d, double* X, double* Y, double** outs) {
+    double* a = Y;
+    double* b = X;
+    for (int k = 0; k < d - 1; ++k) { outs[k] = a; double* t = a; a = b; b = t; }
+    // the last mode reads outs[d-2] (or X when d == 1); the other one is free
+    const double* reads = d >= 2 ? outs[d - 2] : X;
+    return reads == X ? Y : X;
+}
+
+PointwiseG pointwise_of(const mm_nonlin* g) {
+    PointwiseG pg{};
+    pg.kind = MM_G_NONE;
+    if (!g) return pg;
+    if (g->kind == MM_G_CUBIC || g->kind == MM_G_ADR_MANUFACTURED) {
+        pg.kind = g->kind;
+        pg.c0 = g->c[0]; pg.c1 = g->c[1]; pg.c2 = g->c[2]; pg.c3 = g->c[3];
+        pg.psi_a = g->psi_a; pg.psi_b = g->psi_b;
+    }
+    return pg;
+}
+
+StencilArgs stencil_base(const mm_plan_s* p, const double* U, double* W, int mode, double t,
+                         const PointwiseG& pg) {
+    StencilArgs a{};
+    a.mode = mode; a.d = p->d; a.N = p->N;
+    int64_t st = 1;
+    for (int mu = 0; mu < p->d; ++mu) {
+        a.n[mu] = p->n[mu];
+        a.stride[mu] = st;
+        st *= p->n[mu];
+        a.diag3[mu] = p->diag3[mu];
+    }
+    a.U = U; a.W = W; a.t = t; a.g = pg;
+    return a;
+}
+
+// Plain n x n-type GEMM C = A*B (+ D1*beta + D2*gamma), column-major.
+int plain_gemm(int M, int N, int K, const double* A, int64_t lda, const double* B, int64_t ldb,
+               double* C, int64_t ldc, const double* D1, double beta, const double* D2, double gamma,
+               cudaStream_t s) {
+    Gemm g{};
+    g.M = M; g.N = N; g.K = K; g.batch = 1;
+    g.A = A; g.lda = lda; g.B = B; g.ldb = ldb; g.b_kcontig = 1; g.ldc = ldc;
+    Epi e{};
+    e.kind = EPI_STORE; e.alpha = 1.0; e.C = C;
+    e.D1 = D1; e.beta = beta; e.D2 = D2; e.gamma = gamma;
+    return launch_dgemm(g, e, s);
+}
+
+// Riccati G(U) = C + (U B) U (eq. (2)) with U n1 x n2: XB = U B, G = XB U + C + gamma*D2.
+int riccati_g(const mm_plan_s* p, const mm_nonlin* g, const double* U, double* XB, double* G,
+              const double* D2, double gamma, cudaStream_t s) {
+    const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+    int rc = plain_gemm(n1, n1, n2, U, n1, g->B, n2, XB, n1, nullptr, 0, nullptr, 0, s);
+    if (rc) return rc;
+    return plain_gemm(n1, n2, n1, XB, n1, U, n1, G, n1, g->C, 1.0, D2, gamma, s);
+}
+
+// W = K U + G(t, U).  For Riccati, G is also left in Gn.
+int ku_plus_g(mm_plan_s* p, const mm_nonlin* g, const double* U, double t, double* W, double* Gn,
+              double* XB, cudaStream_t s) {
+    const PointwiseG pg = pointwise_of(g);
+    const bool riccati = g && g->kind == MM_G_RICCATI;
+    int rc;
+    if (riccati) {
+        rc = riccati_g(p, g, U, XB, Gn, nullptr, 0.0, s);
+        if (rc) return rc;
+    } else if (p->tridiag) {
+        return launch_prepass(stencil_base(p, U, W, PRE_KU_G, t, pg), s);
+    } else {
+        rc = launch_prepass(stencil_base(p, U, W, PRE_G, t, pg), s);
+        if (rc) return rc;
+    }
+    // dense K u accumulated into W: W = U x_1 A_1 + (Gn or W), then W += U x_mu A_mu
+    for (int mu = 1; mu <= p->d; ++mu) {
+        Gemm gm = mode_gemm(p->d, p->n, mu, p->A[mu - 1], U);
+        Epi e{};
+        e.kind = EPI_STORE; e.alpha = 1.0; e.C = W;
+        e.D1 = (mu == 1 && riccati) ? Gn : W;
+        e.beta = 1.0;
+        rc = launch_dgemm(gm, e, s);
+        if (rc) return rc;
+    }
+    return MM_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    const char* x = (const char*)a;
+    const char* y = (const char*)b;
+    return a && b && x < y + nb && y < x + na;
+}
+
+int scheme_ell(int scheme) {
+    switch (scheme) {
+    case MM_EXPEULER: return 1;
+    case MM_ETD2RK: return 2;
+    case MM_LAWSON_EULER: return 0;
+    case MM_LAWSON2B: return 0;
+    default: return -1;
+    }
+}
+
+}  // namespace
+
+}  // namespace mm
+
+using namespace mm;
+
+extern "C" size_t mumode_workspace_bytes(mm_plan p) {
+    if (!p) return 0;
+    return p->d >= 2 ? (size_t)p->N * sizeof(double) : 0;
+}
+
+extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, double alpha,
+                                void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !V || !P || ell < 0 || ell > p->ell_max || !isfinite(alpha)) return MM_ERR_ARG;
+    const size_t bytes = (size_t)p->N * sizeof(double);
+    if (overlaps(V, bytes, P, bytes)) return MM_ERR_ARG;
+    const size_t need = mumode_workspace_bytes(p);
+    if (need && (!ws || ws_bytes < need || ((uintptr_t)ws & 7))) return MM_ERR_WORKSPACE;
+    if (need && (overlaps(ws, need, V, bytes) || overlaps(ws, need, P, bytes))) return MM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* T = (double*)ws;
+    double* outs[MM_MAX_D];
+    // mode d writes P; mode d-1 writes T; earlier modes alternate backwards
+    for (int k = 0; k < p->d - 1; ++k) outs[k] = ((p->d - 2 - k) % 2 == 0) ? T : P;
+    Epi last{};
+    last.kind = EPI_STORE;
+    last.alpha = alpha * pow(factorial(ell), p->d - 1);
+    last.C = P;
+    return tucker_chain(p, ell, V, outs, last, s);
+}
+
+extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g) {
+    if (!p) return 0;
+    const size_t N = (size_t)p->N;
+    size_t buffers = 2;                          // Tucker ping-pong X, Y
+    if (scheme == MM_ETD2RK) buffers = 3;        // + U2
+    if (scheme == MM_LAWSON2B) buffers = 4;      // + Z, U2
+    size_t elems = buffers * N;
+    if (g && g->kind == MM_G_RICCATI && p->d == 2) {
+        const size_t n1 = (size_t)p->n[0];
+        elems += N + (n1 * n1 > N ? n1 * n1 : N);  // Gn, XB
+    }
+    return elems * sizeof(double);
+}
+
+extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,
+                           int nsteps, void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !U || nsteps < 0 || !isfinite(t0)) return MM_ERR_ARG;
+    const int ell = scheme_ell(scheme);
+    if (ell < 0) return MM_ERR_ARG;
+    if (ell > p->ell_max) return MM_ERR_ARG;
+    const int gk = g ? g->kind : MM_G_NONE;
+    if (gk < MM_G_NONE || gk > MM_G_ADR_MANUFACTURED) return MM_ERR_ARG;
+    if (gk == MM_G_RICCATI) {
+        if (p->d != 2 || !g->B || !g->C) return MM_ERR_ARG;
+        if (scheme != MM_EXPEULER && scheme != MM_ETD2RK) return MM_ERR_UNSUPPORTED;
+    }
+    if (gk == MM_G_ADR_MANUFACTURED && (!g->psi_a || !g->psi_b)) return MM_ERR_ARG;
+    const size_t need = expint_workspace_bytes(p, scheme, g);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 7)) return MM_ERR_WORKSPACE;
+    const size_t bytes = (size_t)p->N * sizeof(double);
+    if (overlaps(ws, need, U, bytes)) return MM_ERR_ARG;
+    if (nsteps == 0) return MM_OK;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = p->N;
+    double* X = (double*)ws;
+    double* Y = X + N;
+    double* U2 = Y + N;                                     // ETD2RK, Lawson2b
+    double* Z = (scheme == MM_LAWSON2B) ? U2 + N : nullptr; // Lawson2b second input
+    double* extra = X + (scheme == MM_ETD2RK ? 3 : (scheme == MM_LAWSON2B ? 4 : 2)) * N;
+    double* Gn = extra;                                     // Riccati
+    double* XB = extra + N;
+    const PointwiseG pg = pointwise_of(g);
+    const double tau = p->tau;
+    const int d = p->d;
+    double* outs[MM_MAX_D];
+    int rc = MM_OK;
+
+    for (int k = 0; k < nsteps && rc == MM_OK; ++k) {
+        const double t = t0 + k * tau;
+        switch (scheme) {
+        case MM_EXPEULER: {
+            rc = ku_plus_g(p, g, U, t, X, Gn, XB, s);
+            if (rc) break;
+            ping_pong(d, X, Y, outs);
+            Epi e{};
+            e.kind = EPI_EE; e.alpha = tau; e.U = U; e.status = p->status;
+            rc = tucker_chain(p, 1, X, outs, e, s);
+            break;
+        }
+        case MM_ETD2RK: {
+            rc = ku_plus_g(p, g, U, t, X, Gn, XB, s);
+            if (rc) break;
+            double* freebuf = ping_pong(d, X, Y, outs);
+            Epi e1{};
+            e1.U = U; e1.U2 = U2; e1.alpha = tau; e1.t0 = t; e1.t1 = t + tau; e1.g = pg;
+            e1.status = p->status;
+            double* W2 = freebuf;
+            if (gk == MM_G_RICCATI) {
+                e1.kind = EPI_ETD_S1_NOG;
+            } else {
+                e1.kind = EPI_ETD_S1;
+                e1.W2 = W2;
+            }
+            rc = tucker_chain(p, 1, X, outs, e1, s);
+            if (rc) break;
+            if (gk == MM_G_RICCATI) {
+                // W2 = G(U2) - G(U) = (U2 B) U2 + C - Gn
+                rc = riccati_g(p, g, U2, XB, W2, Gn, -1.0, s);
+                if (rc) break;
+            }
+            double* other = (W2 == X) ? Y : X;
+            ping_pong(d, W2, other, outs);
+            Epi e2{};
+            e2.kind = EPI_ETD_S2; e2.alpha = tau * pow(2.0, d - 1); e2.U = U; e2.U2 = U2;
+            e2.status = p->status;
+            rc = tucker_chain(p, 2, W2, outs, e2, s);
+            break;
+        }
+        case MM_LAWSON_EULER: {
+            StencilArgs a = stencil_base(p, U, X, PRE_LAWSON, t, pg);
+            a.ca = tau;
+            rc = launch_prepass(a, s);
+            if (rc) break;
+            ping_pong(d, X, Y, outs);
+            Epi e{};
+            e.kind = EPI_STORE; e.alpha = 1.0; e.C = U;
+            rc = tucker_chain(p, 0, X, outs, e, s);
+            break;
+        }
+        case MM_LAWSON2B: {
+            StencilArgs a = stencil_base(p, U, X, PRE_LAWSON, t, pg);
+            a.ca = tau; a.cb = 0.5 * tau; a.W2 = Z;
+            rc = launch_prepass(a, s);
+            if (rc) break;
+            ping_pong(d, X, Y, outs);
+            Epi e1{};
+            e1.kind = EPI_STORE; e1.alpha = 1.0; e1.C = U2;
+            rc = tucker_chain(p, 0, X, outs, e1, s);
+            if (rc) break;
+            ping_pong(d, Z, Y, outs);
+            Epi e2{};
+            e2.kind = EPI_LAWSON2; e2.alpha = 1.0; e2.beta = 0.5 * tau; e2.U = U; e2.U2 = U2;
+            e2.t1 = t + tau; e2.g = pg; e2.status = p->status;
+            rc = tucker_chain(p, 0, Z, outs, e2, s);
+            break;
+        }
+        default: rc = MM_ERR_ARG;
+        }
+    }
+    return rc;
+}

@@ -1,0 +1,48 @@
+// The plan object behind the opaque mm_plan handle.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct mm_graph_cache {
+    cudaGraphExec_t exec = nullptr;
+    int scheme = -1;
+    const void* key[8] = {};
+    double t0 = 0.0;
+};
+
+struct mm_plan_s {
+    int d = 0;
+    int64_t n[MM_MAX_D] = {};
+    int64_t N = 0;
+    int ell_max = 0;
+    int prec = MM_FP64;
+    double tau = 0.0;
+    int owner[MM_MAX_D] = {};          // direction whose phi set is shared
+    int squarings[MM_MAX_D] = {};
+    int tridiag = 1;                   // every A_mu has band width <= 1
+    double* A[MM_MAX_D] = {};          // device copy of A_mu (column-major)
+    double* diag3[MM_MAX_D] = {};      // [sub | main | super] of A_mu
+    double* phi[MM_MAX_D][4] = {};     // phi_l(tau A_mu), FP64, column-major
+    // TF32x3 form: per direction and l, the pre-split operand images the
+    // tensor-core kernel loads (layout in tf32.cu).
+    float* phi_split[MM_MAX_D][4] = {};
+    unsigned int* status = nullptr;    // device status word (MM_STATUS_* bits)
+    std::vector<void*> owned;
+
+    bool alloc(void** p, size_t bytes) {
+        if (cudaMalloc(p, bytes) != cudaSuccess) { *p = nullptr; return false; }
+        owned.push_back(*p);
+        return true;
+    }
+    ~mm_plan_s() {
+        for (void* q : owned) cudaFree(q);
+        if (status) cudaFree(status);
+    }
+};
+
+namespace mm {
+// Builds the TF32x3 operand images of the plan's phi matrices (tf32.cu).
+int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s);
+}  // namespace mm

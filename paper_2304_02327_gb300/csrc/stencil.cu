@@ -1,0 +1,65 @@
+// Pointwise prepasses of the integrators (FP64, HBM-bound).
+//
+//   PRE_KU_G     W = sum_mu U x_mu A_mu + g(t, U)     for tridiagonal A_mu (the
+//                centred-difference operators of Section 4.2): K u is formed
+//                without assembling K (Section 3.2) as a 3-point stencil per
+//                direction, read from the diagonals of A_mu.
+//   PRE_G        W = g(t, U)                           (dense A_mu: the mode
+//                products then accumulate K u into W)
+//   PRE_LAWSON   W = U + a g(t, U);  W2 = U + b g(t, U) (if W2 != NULL)
+//
+// One CTA walks rows of the fastest index i_1, so loads and stores are
+// coalesced and the neighbours along i_2.. i_d come from L1/L2.
+#include "common.cuh"
+#include "stencil.cuh"
+
+namespace mm {
+
+namespace {
+
+__global__ void __launch_bounds__(256) prepass_kernel(StencilArgs a) {
+    const int64_t rows = a.N / a.n[0];
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        // multi-index of this row in directions 2..d
+        int idx[MM_MAX_D];
+        int64_t rem = row;
+        for (int mu = 1; mu < a.d; ++mu) { idx[mu] = (int)(rem % a.n[mu]); rem /= a.n[mu]; }
+        const int64_t base = row * a.n[0];
+        for (int i1 = threadIdx.x; i1 < a.n[0]; i1 += blockDim.x) {
+            const int64_t off = base + i1;
+            const double u = a.U[off];
+            const double g = g_point(a.g, u, a.t, off);
+            if (a.mode == PRE_KU_G) {
+                double acc = g;
+                idx[0] = i1;
+                for (int mu = 0; mu < a.d; ++mu) {
+                    const int i = idx[mu];
+                    const int nm = (int)a.n[mu];
+                    const double* dg = a.diag3[mu];
+                    acc = fma(dg[nm + i], u, acc);
+                    if (i > 0) acc = fma(dg[i], a.U[off - a.stride[mu]], acc);
+                    if (i + 1 < nm) acc = fma(dg[2 * nm + i], a.U[off + a.stride[mu]], acc);
+                }
+                a.W[off] = acc;
+            } else if (a.mode == PRE_G) {
+                a.W[off] = g;
+            } else {
+                a.W[off] = fma(a.ca, g, u);
+                if (a.W2) a.W2[off] = fma(a.cb, g, u);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int launch_prepass(const StencilArgs& a, cudaStream_t s) {
+    const int64_t rows = a.N / a.n[0];
+    int64_t grid = rows < 65535LL * 16 ? rows : 65535LL * 16;
+    int block = a.n[0] >= 256 ? 256 : (a.n[0] >= 128 ? 128 : (a.n[0] >= 64 ? 64 : 32));
+    prepass_kernel<<<(unsigned)grid, block, 0, s>>>(a);
+    MM_LAUNCH_CHECK();
+    return MM_OK;
+}
+
+}  // namespace mm
