@@ -192,6 +192,26 @@ MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
 MM_API int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,
                 int nsteps, void* ws, size_t ws_bytes, void* stream);
 
+/* ---- launch tracing --------------------------------------------------
+ * Kernel classes counted by the library.  Counting is always on; with tracing
+ * enabled every launch is also bracketed by a pair of CUDA events recorded on
+ * the stream it is launched on (not while that stream is being captured).   */
+#define MM_KC_CONTRACT_FP64 0   /* FP64 mu-mode / plain contraction kernel     */
+#define MM_KC_CONTRACT_TF32 1   /* TF32x3 tcgen05 mu-mode contraction kernel   */
+#define MM_KC_PREPASS       2   /* K u + g stencil / pointwise prepass         */
+#define MM_KC_SPLIT         3   /* FP64 -> TF32 hi/lo operand split            */
+#define MM_KC_COUNT         4
+
+/* Start a new window: zero the counters; on != 0 also records event pairs.
+ * Host-only, never fails. */
+MM_API int mm_trace_enable(int on);
+
+/* Launches of class `cls` in the current window and, if ms != NULL, their summed
+ * device time in milliseconds (synchronises on the recorded events; 0 if
+ * tracing is off).  launches is a host pointer to a long long.
+ * Errors: MM_ERR_ARG (cls out of range), MM_ERR_CUDA. */
+MM_API int mm_trace_read(int cls, long long* launches, double* ms);
+
 /* Human-readable name of a status code (static string). */
 MM_API const char* mm_status_str(int code);
 

@@ -33,7 +33,9 @@ PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3}
 
 EXPORTS = ("phi_plan_create", "phi_plan_destroy", "phi_plan_info", "phi_plan_get_phi",
            "phi_plan_status", "mumode_workspace_bytes", "mumode_phi_apply",
-           "expint_workspace_bytes", "expint_step", "mm_status_str", "mm_version")
+           "expint_workspace_bytes", "expint_step", "mm_status_str", "mm_version",
+           "mm_trace_enable", "mm_trace_read")
+KC_CONTRACT_FP64, KC_CONTRACT_TF32, KC_PREPASS, KC_SPLIT = 0, 1, 2, 3
 
 
 class PhisplitError(RuntimeError):
@@ -78,6 +80,8 @@ def lib():
     L.mm_status_str.argtypes = [i32]
     L.mm_status_str.restype = ctypes.c_char_p
     L.mm_version.argtypes = []
+    L.mm_trace_enable.argtypes = [i32]
+    L.mm_trace_read.argtypes = [i32, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(f64)]
     for name in EXPORTS:
         getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
     _lib = L
@@ -235,6 +239,20 @@ def expint_step(plan: Plan, scheme: int, U: torch.Tensor, nsteps: int, t0: float
     _check(lib().expint_step(plan.handle, int(scheme), gs, _ptr(U), float(t0), int(nsteps),
                              _ptr(ws), ws.numel() * 8, _stream(stream)), "expint_step")
     return U
+
+
+def trace_enable(on: bool = True) -> None:
+    """Start a new tracing window (counts always; event timing if on)."""
+    lib().mm_trace_enable(int(on))
+
+
+def trace_read(cls: int, timed: bool = True):
+    """(launches, device ms) of kernel class cls in the current window."""
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(lib().mm_trace_read(int(cls), ctypes.byref(n), ctypes.byref(ms) if timed else None),
+           "mm_trace_read")
+    return n.value, (ms.value if timed else None)
 
 
 def ell_for_scheme(scheme: int) -> int:

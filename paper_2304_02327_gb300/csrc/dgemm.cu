@@ -11,6 +11,7 @@
 // no transpose pass: the operand whose contiguous index is the output's row
 // index is read directly.
 #include "common.cuh"
+#include "trace.cuh"
 
 namespace mm {
 
@@ -102,6 +103,7 @@ int launch_cfg(const Gemm& g, const Epi& e, cudaStream_t s) {
     int64_t ntiles = (int64_t)tilesM * tilesN * g.batch;
     if (ntiles <= 0) return MM_OK;
     if (ntiles > 0x7fffffffLL) return MM_ERR_SHAPE;
+    TraceScope tr(KC_CONTRACT_FP64, s);
     dgemm_kernel<BM, BN, BK, TM, TN><<<(unsigned)ntiles, (BM / TM) * (BN / TN), 0, s>>>(g, e, tilesM, tilesN);
     MM_LAUNCH_CHECK();
     return MM_OK;

@@ -12,6 +12,7 @@
 // coalesced and the neighbours along i_2.. i_d come from L1/L2.
 #include "common.cuh"
 #include "stencil.cuh"
+#include "trace.cuh"
 
 namespace mm {
 
@@ -57,6 +58,7 @@ int launch_prepass(const StencilArgs& a, cudaStream_t s) {
     const int64_t rows = a.N / a.n[0];
     int64_t grid = rows < 65535LL * 16 ? rows : 65535LL * 16;
     int block = a.n[0] >= 256 ? 256 : (a.n[0] >= 128 ? 128 : (a.n[0] >= 64 ? 64 : 32));
+    TraceScope tr(KC_PREPASS, s);
     prepass_kernel<<<(unsigned)grid, block, 0, s>>>(a);
     MM_LAUNCH_CHECK();
     return MM_OK;
