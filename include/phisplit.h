@@ -192,6 +192,41 @@ MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
 MM_API int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,
                 int nsteps, void* ws, size_t ws_bytes, void* stream);
 
+/* ---- allocation-free Tucker chain ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers of
+ * this library that cannot allocate device memory when they need the split
+ * action: code embedded in a host application that owns every byte of device
+ * memory through its own pool and forbids side allocations, loops with latency
+ * budgets that cannot afford cudaMalloc/cudaFree (both may synchronise the
+ * device), and plug-ins whose process does not let them call the CUDA allocator.
+ *
+ * tucker_apply_noalloc computes, in FP64,
+ *     P = alpha * V x_1 M_1 x_2 M_2 ... x_d M_d
+ * (the same contraction chain as mumode_phi_apply; pass M_mu = phi_l(tau A_mu),
+ * for instance from phi_plan_get_phi, and alpha = alpha' * (l!)^(d-1) to get
+ * P_l^(2)).  Its intermediate tensor lives in one fixed array of
+ * MM_NOALLOC_MAX_ELEMS doubles (16 MiB) compiled into the library, which every
+ * GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   d      1..8;  n: host array of d sizes, 1..8192 each.
+ *   M      host array of d device pointers, M[mu] n_mu x n_mu column-major.
+ *   V, P   device tensors of N = prod n_mu doubles (i_1 fastest); must not
+ *          overlap.  N > MM_NOALLOC_MAX_ELEMS is rejected with MM_ERR_SHAPE
+ *          before any device work.
+ *   stream cudaStream_t as void*; stream-ordered, no synchronisation.
+ * The first call on a device (with that device current) looks up the array's
+ * device address once (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls on a device share the one array and it keeps the
+ * last call's contents (every element is written before it is read, so nothing
+ * needs clearing): calls whose execution overlaps on the GPU -- on different
+ * streams, or from different host threads -- race on it and must be ordered by
+ * the caller.  Errors: MM_ERR_ARG, MM_ERR_SHAPE, MM_ERR_UNSUPPORTED (device
+ * ordinal >= 64), MM_ERR_CUDA. */
+#define MM_NOALLOC_MAX_ELEMS (1LL << 21)
+MM_API int tucker_apply_noalloc(int d, const int64_t* n, const double* const* M,
+                                const double* V, double* P, double alpha, void* stream);
+
 /* ---- launch tracing --------------------------------------------------
  * Kernel classes counted by the library.  Counting is always on; with tracing
  * enabled every launch is also bracketed by a pair of CUDA events recorded on

@@ -34,7 +34,7 @@ PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3}
 EXPORTS = ("phi_plan_create", "phi_plan_destroy", "phi_plan_info", "phi_plan_get_phi",
            "phi_plan_status", "mumode_workspace_bytes", "mumode_phi_apply",
            "expint_workspace_bytes", "expint_step", "mm_status_str", "mm_version",
-           "mm_trace_enable", "mm_trace_read")
+           "mm_trace_enable", "mm_trace_read", "tucker_apply_noalloc")
 KC_CONTRACT_FP64, KC_CONTRACT_TF32, KC_PREPASS, KC_SPLIT = 0, 1, 2, 3
 
 
@@ -80,6 +80,7 @@ def lib():
     L.mm_status_str.argtypes = [i32]
     L.mm_status_str.restype = ctypes.c_char_p
     L.mm_version.argtypes = []
+    L.tucker_apply_noalloc.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp, f64, vp]
     L.mm_trace_enable.argtypes = [i32]
     L.mm_trace_read.argtypes = [i32, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(f64)]
     for name in EXPORTS:
