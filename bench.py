@@ -40,6 +40,7 @@ METRIC = "DOF-steps/s"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2, written between timed steps
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk x 2.07 GHz
 CUBLAS_DGEMM_TFLOPS_MEASURED = 1.10          # torch.matmul float64 8192^3 on this pool
+TF32_NOMINAL_RATIO = 1.1 / 2.25                # nominal dense TF32 / BF16 tensor rate
 
 
 def parse():
@@ -285,7 +286,24 @@ def ours(args):
     achieved = flops_per_launch / (k_ms / n_launch / 1e3) / 1e12 if n_launch else None
     total_launches = sum(v[0] for v in launches.values())
     if tf32:
-        roof = {"bound": "tensor", "unit": "TFLOP/s"}
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        peak = bf16 * TF32_NOMINAL_RATIO
+        tflops = 4 * flops_per_launch      # x_hi*b0 + x_lo*b0 + x_hi*b1 + x_hi*b2 per mode product
+        achieved = tflops / (k_ms / n_launch / 1e3) / 1e12 if n_launch else None
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": profile_traffic("contract_tf32", args.workload),
+                "kernel": "tf32x3_mode_kernel (tcgen05 mu-mode contraction)",
+                "launches": n_launch, "avg_launch_ms": k_ms / n_launch if n_launch else None,
+                "share_of_step_time": k_ms / t_ms if t_ms else None,
+                "flops_per_launch": tflops,
+                "peak_note": f"TF32 dense peak = measured bf16 {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json) "
+                             "x nominal TF32/BF16 ratio 1.1/2.25"}
     else:
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,

@@ -24,6 +24,7 @@ namespace mm {
 struct PointwiseG {
     int kind;                 // MM_G_NONE / MM_G_CUBIC / MM_G_ADR_MANUFACTURED
     double c0, c1, c2, c3;
+    float f0, f1, f2, f3;     // the same coefficients rounded to FP32 (mixed form)
     const double* psi_a;
     const double* psi_b;
 };
@@ -61,6 +62,7 @@ struct Epi {
     double* U;
     double* U2;
     double* W2;
+    float* W2f;         // mixed form: FP32 stage-2 input g(U2) - g(U)
     double t0, t1;
     PointwiseG g;
     unsigned int* status;

@@ -23,36 +23,41 @@ double factorial(int k) {
     return f;
 }
 
-int mode_product(mm_plan_s* p, int ell, int mu, const double* in, const Epi& e, cudaStream_t s) {
-    if (p->prec == MM_TF32X3) return tf32_mode_product(p, ell, mu, in, e, s);
+int fp64_mode_product(mm_plan_s* p, int ell, int mu, const double* in, const Epi& e, cudaStream_t s) {
     Gemm g = mode_gemm(p->d, p->n, mu, p->phi[mu - 1][ell], in);
     return launch_dgemm(g, e, s);
 }
 
-// Modes 1..d-1 store into outs[0..d-2]; mode d applies `last`.
-int tucker_chain(mm_plan_s* p, int ell, const double* in, double* const* outs, const Epi& last,
-                 cudaStream_t s) {
+// FP64 Tucker chain: modes 1..d-1 store into outs[0..d-2]; mode d applies `last`.
+int fp64_chain(mm_plan_s* p, int ell, const double* in, double* const* outs, const Epi& last,
+               cudaStream_t s) {
     const double* cur = in;
     for (int mu = 1; mu < p->d; ++mu) {
         Epi e{};
         e.kind = EPI_STORE;
         e.alpha = 1.0;
         e.C = outs[mu - 1];
-        int rc = mode_product(p, ell, mu, cur, e, s);
+        int rc = fp64_mode_product(p, ell, mu, cur, e, s);
         if (rc) return rc;
         cur = outs[mu - 1];
     }
-    return mode_product(p, ell, p->d, cur, last, s);
+    return fp64_mode_product(p, ell, p->d, cur, last, s);
 }
 
-// Alternating outputs X->Y->X... starting from Y; returns the buffer free in the last mode.
-double* ping_pong(int d, double* X, double* Y, double** outs) {
-    double* a = Y;
-    double* b = X;
-    for (int k = 0; k < d - 1; ++k) { outs[k] = a; double* t = a; a = b; b = t; }
-    // the last mode reads outs[d-2] (or X when d == 1); the other one is free
-    const double* reads = d >= 2 ? outs[d - 2] : X;
-    return reads == X ? Y : X;
+// Tucker of `in` (consumable, N doubles) with scratch (N doubles) and the final
+// epilogue `last`.  The FP64 chain ping-pongs between in and scratch.
+int run_tucker(mm_plan_s* p, int ell, double* in, double* scratch, const Epi& last, cudaStream_t s) {
+    double* outs[MM_MAX_D];
+    for (int k = 0; k < p->d - 1; ++k) outs[k] = (k % 2 == 0) ? scratch : in;
+    return fp64_chain(p, ell, in, outs, last, s);
+}
+
+// The FP64 buffer (in or scratch) that run_tucker leaves untouched while its last
+// mode runs, so the last epilogue may write into it.
+double* free_during_last(const mm_plan_s* p, double* in, double* scratch) {
+    if (p->d == 1) return scratch;
+    // FP64: the last mode reads outs[d-2] = (d-2 even ? scratch : in)
+    return (p->d % 2 == 0) ? in : scratch;
 }
 
 PointwiseG pointwise_of(const mm_nonlin* g) {
@@ -62,6 +67,7 @@ PointwiseG pointwise_of(const mm_nonlin* g) {
     if (g->kind == MM_G_CUBIC || g->kind == MM_G_ADR_MANUFACTURED) {
         pg.kind = g->kind;
         pg.c0 = g->c[0]; pg.c1 = g->c[1]; pg.c2 = g->c[2]; pg.c3 = g->c[3];
+        pg.f0 = (float)g->c[0]; pg.f1 = (float)g->c[1]; pg.f2 = (float)g->c[2]; pg.f3 = (float)g->c[3];
         pg.psi_a = g->psi_a; pg.psi_b = g->psi_b;
     }
     return pg;
@@ -169,14 +175,15 @@ extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, 
     if (need && (overlaps(ws, need, V, bytes) || overlaps(ws, need, P, bytes))) return MM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     double* T = (double*)ws;
-    double* outs[MM_MAX_D];
-    // mode d writes P; mode d-1 writes T; earlier modes alternate backwards
-    for (int k = 0; k < p->d - 1; ++k) outs[k] = ((p->d - 2 - k) % 2 == 0) ? T : P;
     Epi last{};
     last.kind = EPI_STORE;
     last.alpha = alpha * pow(factorial(ell), p->d - 1);
     last.C = P;
-    return tucker_chain(p, ell, V, outs, last, s);
+    if (p->prec == MM_TF32X3) return mixed_tucker(p, ell, V, true, (float*)T, (float*)T + p->N, last, s);
+    double* outs[MM_MAX_D];
+    // mode d writes P; mode d-1 writes T; earlier modes alternate backwards
+    for (int k = 0; k < p->d - 1; ++k) outs[k] = ((p->d - 2 - k) % 2 == 0) ? T : P;
+    return fp64_chain(p, ell, V, outs, last, s);
 }
 
 extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g) {
@@ -213,6 +220,10 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     if (nsteps == 0) return MM_OK;
 
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->prec == MM_TF32X3) {
+        if (gk == MM_G_RICCATI) return MM_ERR_UNSUPPORTED;
+        return mixed_expint(p, scheme, pointwise_of(g), U, t0, nsteps, (double*)ws, s);
+    }
     const int64_t N = p->N;
     double* X = (double*)ws;
     double* Y = X + N;
@@ -224,7 +235,6 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     const PointwiseG pg = pointwise_of(g);
     const double tau = p->tau;
     const int d = p->d;
-    double* outs[MM_MAX_D];
     int rc = MM_OK;
 
     for (int k = 0; k < nsteps && rc == MM_OK; ++k) {
@@ -233,16 +243,15 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
         case MM_EXPEULER: {
             rc = ku_plus_g(p, g, U, t, X, Gn, XB, s);
             if (rc) break;
-            ping_pong(d, X, Y, outs);
             Epi e{};
             e.kind = EPI_EE; e.alpha = tau; e.U = U; e.status = p->status;
-            rc = tucker_chain(p, 1, X, outs, e, s);
+            rc = run_tucker(p, 1, X, Y, e, s);
             break;
         }
         case MM_ETD2RK: {
             rc = ku_plus_g(p, g, U, t, X, Gn, XB, s);
             if (rc) break;
-            double* freebuf = ping_pong(d, X, Y, outs);
+            double* freebuf = free_during_last(p, X, Y);
             Epi e1{};
             e1.U = U; e1.U2 = U2; e1.alpha = tau; e1.t0 = t; e1.t1 = t + tau; e1.g = pg;
             e1.status = p->status;
@@ -253,7 +262,7 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
                 e1.kind = EPI_ETD_S1;
                 e1.W2 = W2;
             }
-            rc = tucker_chain(p, 1, X, outs, e1, s);
+            rc = run_tucker(p, 1, X, Y, e1, s);
             if (rc) break;
             if (gk == MM_G_RICCATI) {
                 // W2 = G(U2) - G(U) = (U2 B) U2 + C - Gn
@@ -261,11 +270,10 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
                 if (rc) break;
             }
             double* other = (W2 == X) ? Y : X;
-            ping_pong(d, W2, other, outs);
             Epi e2{};
             e2.kind = EPI_ETD_S2; e2.alpha = tau * pow(2.0, d - 1); e2.U = U; e2.U2 = U2;
             e2.status = p->status;
-            rc = tucker_chain(p, 2, W2, outs, e2, s);
+            rc = run_tucker(p, 2, W2, other, e2, s);
             break;
         }
         case MM_LAWSON_EULER: {
@@ -273,10 +281,9 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
             a.ca = tau;
             rc = launch_prepass(a, s);
             if (rc) break;
-            ping_pong(d, X, Y, outs);
             Epi e{};
             e.kind = EPI_STORE; e.alpha = 1.0; e.C = U;
-            rc = tucker_chain(p, 0, X, outs, e, s);
+            rc = run_tucker(p, 0, X, Y, e, s);
             break;
         }
         case MM_LAWSON2B: {
@@ -284,16 +291,14 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
             a.ca = tau; a.cb = 0.5 * tau; a.W2 = Z;
             rc = launch_prepass(a, s);
             if (rc) break;
-            ping_pong(d, X, Y, outs);
             Epi e1{};
             e1.kind = EPI_STORE; e1.alpha = 1.0; e1.C = U2;
-            rc = tucker_chain(p, 0, X, outs, e1, s);
+            rc = run_tucker(p, 0, X, Y, e1, s);
             if (rc) break;
-            ping_pong(d, Z, Y, outs);
             Epi e2{};
             e2.kind = EPI_LAWSON2; e2.alpha = 1.0; e2.beta = 0.5 * tau; e2.U = U; e2.U2 = U2;
             e2.t1 = t + tau; e2.g = pg; e2.status = p->status;
-            rc = tucker_chain(p, 0, Z, outs, e2, s);
+            rc = run_tucker(p, 0, Z, Y, e2, s);
             break;
         }
         default: rc = MM_ERR_ARG;

@@ -1,0 +1,109 @@
+// Device helpers of the mixed-precision (TF32x3) form.
+//
+// On GB300 the FP64 pipe issues ~2 operations per clock per SM against 128 for
+// FP32, so one FP64 operation per element of a 32.8M-element state costs as much
+// as the whole tensor-core contraction of a mode.  The mixed form therefore
+// touches the FP64 pipe only for the state update u + tau*y; conversions between
+// FP64 and FP32 are done exactly with integer bit manipulation, and everything
+// else (K u, g, the split into TF32 parts, partial-sum combination) runs in FP32.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace mm {
+namespace mx {
+
+// Exact widening FP32 -> FP64 by bit manipulation (FP32 subnormals flush to 0).
+__device__ __forceinline__ double f2d(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint64_t s = (uint64_t)(b >> 31) << 63;
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint64_t m = (uint64_t)(b & 0x7fffffu) << 29;
+    if (e == 0) return __longlong_as_double((long long)s);
+    if (e == 0xffu) return __longlong_as_double((long long)(s | 0x7ff0000000000000ull | m));
+    return __longlong_as_double((long long)(s | ((uint64_t)(e + 896u) << 52) | m));
+}
+
+// x ~ hi + lo with hi = x truncated to 24 significant bits and lo = the next 23
+// bits (|x - hi - lo| <= 2^-46 |x|), from the bits of x, without FP64 arithmetic.
+// |x| < 2^-103 gives lo = 0; |x| < 2^-126 gives hi = lo = 0; inf/nan map to inf/nan.
+__device__ __forceinline__ void d2ff(double x, float& hi, float& lo) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t s = (uint32_t)(b >> 63) << 31;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const uint64_t m = b & 0xfffffffffffffull;
+    const int ef = e - 896;                     // FP32 exponent field of x
+    if (ef <= 0) { hi = __uint_as_float(s); lo = 0.f; return; }
+    if (ef >= 255) {                            // overflow -> inf; nan stays nan
+        hi = __uint_as_float(s | 0x7f800000u | ((e == 0x7ff && m) ? 0x400000u : 0u));
+        lo = 0.f;
+        return;
+    }
+    hi = __uint_as_float(s | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
+    if (ef < 24) { lo = 0.f; return; }
+    // remainder = (m mod 2^29) * 2^(e-1075); its top 23 bits as P - Q with
+    // Q = 2^(ef-23-127), P = Q (1 + r/2^23): exact by Sterbenz.
+    const uint32_t r = (uint32_t)((m & 0x1fffffffull) >> 6);
+    const uint32_t E0 = (uint32_t)(ef - 23);
+    const float P = __uint_as_float((E0 << 23) | r);
+    const float Q = __uint_as_float(E0 << 23);
+    lo = __uint_as_float(__float_as_uint(P - Q) | s);
+}
+
+// Round-to-nearest (ties away) FP32 -> TF32, kept in an FP32 container.
+__device__ __forceinline__ float tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// x = hi + lo with hi, lo TF32 (|x - hi - lo| <= 2^-22 |x|).
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    hi = tf32(x);
+    lo = tf32(x - hi);
+}
+__device__ __forceinline__ void split_tf32(double x, float& hi, float& lo) {
+    float a, b;
+    d2ff(x, a, b);
+    hi = tf32(a);
+    lo = tf32((a - hi) + b);
+}
+
+// Pointwise g in FP32 at (t, u): cubic or the manufactured ADR term.
+__device__ __forceinline__ float g32(const PointwiseG& g, float u, float t, int64_t idx) {
+    if (g.kind == MM_G_CUBIC) {
+        return fmaf(fmaf(fmaf(g.f3, u, g.f2), u, g.f1), u, g.f0);
+    } else if (g.kind == MM_G_ADR_MANUFACTURED) {
+        const float et = __expf(t);
+        float ah, al, bh, bl;
+        d2ff(g.psi_a[idx], ah, al);
+        d2ff(g.psi_b[idx], bh, bl);
+        return 1.f / (1.f + u * u) + et * ah - 1.f / (1.f + et * et * bh * bh);
+    }
+    return 0.f;
+}
+
+// g(t1, u + delta) - g(t0, u) in FP32 with relative accuracy in the difference
+// itself: for the cubic c0 + c1 u + c2 u^2 + c3 u^3 the difference is written as
+// delta (c1 + c2 (2u + delta) + c3 (3u^2 + 3u delta + delta^2)), with no
+// cancellation between two nearby values of g.
+__device__ __forceinline__ float dg32(const PointwiseG& g, float u, float delta, float t0, float t1,
+                                      int64_t idx) {
+    if (g.kind == MM_G_CUBIC) {
+        const float q = fmaf(3.f * u, u + delta, delta * delta);
+        return delta * fmaf(g.f3, q, fmaf(g.f2, 2.f * u + delta, g.f1));
+    } else if (g.kind == MM_G_ADR_MANUFACTURED) {
+        return g32(g, u + delta, t1, idx) - g32(g, u, t0, idx);
+    }
+    return 0.f;
+}
+
+// Finite test of a double from its exponent bits (no FP64 pipe).
+__device__ __forceinline__ bool finite_bits(double v) {
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+
+}  // namespace mx
+}  // namespace mm

@@ -28,6 +28,7 @@ struct mm_plan_s {
     // TF32x3 form: per direction and l, the pre-split operand images the
     // tensor-core kernel loads (layout in tf32.cu).
     float* phi_split[MM_MAX_D][4] = {};
+    float* coef3f[MM_MAX_D] = {};      // mixed K u stencil: [a | c | row sum] per direction
     unsigned int* status = nullptr;    // device status word (MM_STATUS_* bits)
     std::vector<void*> owned;
 

@@ -13,6 +13,7 @@
 #include "common.cuh"
 #include "stencil.cuh"
 #include "trace.cuh"
+#include "mixed.cuh"
 
 namespace mm {
 
@@ -52,7 +53,75 @@ __global__ void __launch_bounds__(256) prepass_kernel(StencilArgs a) {
     }
 }
 
+__global__ void __launch_bounds__(256) prepass_mixed_kernel(StencilArgsMixed a) {
+    const int64_t rows = a.N / a.n[0];
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        int idx[MM_MAX_D];
+        int64_t rem = row;
+        for (int mu = 1; mu < a.d; ++mu) { idx[mu] = (int)(rem % a.n[mu]); rem /= a.n[mu]; }
+        const int64_t base = row * a.n[0];
+        for (int i1 = threadIdx.x; i1 < a.n[0]; i1 += blockDim.x) {
+            const int64_t off = base + i1;
+            float uh, ul;
+            mx::d2ff(a.U[off], uh, ul);
+            const float u = uh + ul;
+            const float g = mx::g32(a.g, u, a.t, off);
+            if (a.mode == PRE_KU_G) {
+                float acc = g;
+                idx[0] = i1;
+                for (int mu = 0; mu < a.d; ++mu) {
+                    const int i = idx[mu];
+                    const int nm = (int)a.n[mu];
+                    const float* cf = a.coef[mu];
+                    acc = fmaf(cf[2 * nm + i], u, acc);
+                    if (i > 0) {
+                        float vh, vl;
+                        mx::d2ff(a.U[off - a.stride[mu]], vh, vl);
+                        acc = fmaf(cf[i], (vh - uh) + (vl - ul), acc);
+                    }
+                    if (i + 1 < nm) {
+                        float vh, vl;
+                        mx::d2ff(a.U[off + a.stride[mu]], vh, vl);
+                        acc = fmaf(cf[nm + i], (vh - uh) + (vl - ul), acc);
+                    }
+                }
+                a.Wf[off] = acc;
+            } else {
+                a.Wf[off] = fmaf(a.ca, g, uh) + ul;
+                if (a.W2f) a.W2f[off] = fmaf(a.cb, g, uh) + ul;
+            }
+        }
+    }
+}
+
+__global__ void stencil_coef_kernel(const double* __restrict__ A, int n, float* coef) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double a = i > 0 ? A[i + (int64_t)n * (i - 1)] : 0.0;
+        const double b = A[i + (int64_t)n * i];
+        const double c = i + 1 < n ? A[i + (int64_t)n * (i + 1)] : 0.0;
+        coef[i] = (float)a;
+        coef[n + i] = (float)c;
+        coef[2 * n + i] = (float)((a + b) + c);
+    }
+}
+
 }  // namespace
+
+int launch_prepass_mixed(const StencilArgsMixed& a, cudaStream_t s) {
+    const int64_t rows = a.N / a.n[0];
+    int64_t grid = rows < 65535LL * 16 ? rows : 65535LL * 16;
+    int block = a.n[0] >= 256 ? 256 : (a.n[0] >= 128 ? 128 : (a.n[0] >= 64 ? 64 : 32));
+    TraceScope tr(KC_PREPASS, s);
+    prepass_mixed_kernel<<<(unsigned)grid, block, 0, s>>>(a);
+    MM_LAUNCH_CHECK();
+    return MM_OK;
+}
+
+int build_stencil_coef(const double* A, int n, float* coef, cudaStream_t s) {
+    stencil_coef_kernel<<<(n + 255) / 256, 256, 0, s>>>(A, n, coef);
+    MM_LAUNCH_CHECK();
+    return MM_OK;
+}
 
 int launch_prepass(const StencilArgs& a, cudaStream_t s) {
     const int64_t rows = a.N / a.n[0];

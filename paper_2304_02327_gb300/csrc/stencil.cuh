@@ -23,4 +23,29 @@ struct StencilArgs {
 
 int launch_prepass(const StencilArgs& a, cudaStream_t s);
 
+// Mixed-precision prepass (FP32 output from the FP64 state, no FP64 arithmetic):
+//   PRE_KU_G:   Wf = K u + g(t, u), K tridiagonal, written as
+//               sum_mu a (u_{i-1} - u_i) + c (u_{i+1} - u_i) + s u_i with the row
+//               sums s = a + b + c, the differences taken from the double-float
+//               split of the state (so they keep their own relative accuracy)
+//   PRE_LAWSON: Wf = u + ca g(t, u);  W2f = u + cb g(t, u) (if W2f != NULL)
+struct StencilArgsMixed {
+    int mode;
+    int d;
+    int64_t N;
+    int64_t n[MM_MAX_D];
+    int64_t stride[MM_MAX_D];
+    const float* coef[MM_MAX_D];    // [a | c | s] per direction, 3 n floats
+    const double* U;
+    float* Wf;
+    float* W2f;
+    float t, ca, cb;
+    PointwiseG g;
+};
+
+int launch_prepass_mixed(const StencilArgsMixed& a, cudaStream_t s);
+
+// [a | c | s] floats of a column-major tridiagonal n x n matrix (plan set-up).
+int build_stencil_coef(const double* A, int n, float* coef, cudaStream_t s);
+
 }  // namespace mm
