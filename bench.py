@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="adr3d_n128_etd2rk")
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "bf16x3"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -279,7 +279,7 @@ def ours(args):
         return 0
 
     # ---- roofline of the dominant kernel (the mu-mode contraction) ----
-    tf32 = args.prec == "tf32x3"
+    tf32 = args.prec in ("tf32x3", "bf16x3")
     kc = api.KC_CONTRACT_TF32 if tf32 else api.KC_CONTRACT_FP64
     n_launch, k_ms = launches[kc]
     flops_per_launch = 2.0 * N * (sum(p.n) / len(p.n))   # 2 N n_mu per mode product
@@ -292,8 +292,10 @@ def ours(args):
         except Exception:
             pass
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        peak = bf16 * TF32_NOMINAL_RATIO
-        tflops = 4 * flops_per_launch      # x_hi*b0 + x_lo*b0 + x_hi*b1 + x_hi*b2 per mode product
+        peak = bf16 * TF32_NOMINAL_RATIO if args.prec == "tf32x3" else bf16
+        # MMA products per mode: TF32x3 4 (a0b0 a1b0 a0b1 a0b2), BF16x3 6 (+ a2b0 a1b1)
+        nprod = 4 if args.prec == "tf32x3" else 6
+        tflops = nprod * flops_per_launch
         achieved = tflops / (k_ms / n_launch / 1e3) / 1e12 if n_launch else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
@@ -302,8 +304,9 @@ def ours(args):
                 "launches": n_launch, "avg_launch_ms": k_ms / n_launch if n_launch else None,
                 "share_of_step_time": k_ms / t_ms if t_ms else None,
                 "flops_per_launch": tflops,
-                "peak_note": f"TF32 dense peak = measured bf16 {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json) "
-                             "x nominal TF32/BF16 ratio 1.1/2.25"}
+                "peak_note": (f"TF32 dense peak = measured bf16 {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json) "
+                              "x nominal TF32/BF16 ratio 1.1/2.25") if args.prec == "tf32x3" else
+                             f"BF16 dense peak measured {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json)"}
     else:
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
@@ -319,7 +322,7 @@ def ours(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.prec == "fp64" else "tf32x3+f64",
+        "dtype": "f64" if args.prec == "fp64" else f"{args.prec}+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n": p.n, "N": N,
                    "scheme": wl.SCHEME_NAMES[p.scheme], "tau": p.tau, "precision": args.prec,

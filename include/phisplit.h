@@ -67,6 +67,7 @@ extern "C" {
 /* ---- precision forms ------------------------------------------------- */
 #define MM_FP64    0
 #define MM_TF32X3  1
+#define MM_BF16X3  2
 
 /* ---- time-stepping schemes (Section 2 and Section 3.2) ----------------- */
 #define MM_EXPEULER     0   /* eq. (11) / tensor form eq. (19)               */

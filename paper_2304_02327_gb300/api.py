@@ -25,11 +25,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libphisplit.so")
 
 MM_OK = 0
-MM_FP64, MM_TF32X3 = 0, 1
+MM_FP64, MM_TF32X3, MM_BF16X3 = 0, 1, 2
 EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B = 0, 1, 2, 3
 G_NONE, G_CUBIC, G_RICCATI, G_ADR_MANUFACTURED = 0, 1, 2, 3
 STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2
-PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3}
+PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3, "bf16x3": MM_BF16X3}
 
 EXPORTS = ("phi_plan_create", "phi_plan_destroy", "phi_plan_info", "phi_plan_get_phi",
            "phi_plan_status", "mumode_workspace_bytes", "mumode_phi_apply",

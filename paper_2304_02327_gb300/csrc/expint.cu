@@ -179,7 +179,7 @@ extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, 
     last.kind = EPI_STORE;
     last.alpha = alpha * pow(factorial(ell), p->d - 1);
     last.C = P;
-    if (p->prec == MM_TF32X3) return mixed_tucker(p, ell, V, true, (float*)T, (float*)T + p->N, last, s);
+    if (p->prec != MM_FP64) return mixed_tucker(p, ell, V, true, (float*)T, (float*)T + p->N, last, s);
     double* outs[MM_MAX_D];
     // mode d writes P; mode d-1 writes T; earlier modes alternate backwards
     for (int k = 0; k < p->d - 1; ++k) outs[k] = ((p->d - 2 - k) % 2 == 0) ? T : P;
@@ -220,7 +220,7 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     if (nsteps == 0) return MM_OK;
 
     cudaStream_t s = (cudaStream_t)stream;
-    if (p->prec == MM_TF32X3) {
+    if (p->prec != MM_FP64) {
         if (gk == MM_G_RICCATI) return MM_ERR_UNSUPPORTED;
         return mixed_expint(p, scheme, pointwise_of(g), U, t0, nsteps, (double*)ws, s);
     }

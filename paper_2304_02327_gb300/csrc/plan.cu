@@ -201,7 +201,7 @@ extern "C" int phi_plan_create(mm_plan* out, int d, const int64_t* n, const doub
     *out = nullptr;
     if (!n || !A || d < 1 || d > MM_MAX_D || ell_max < 0 || ell_max > 3 || !isfinite(tau))
         return MM_ERR_ARG;
-    if (prec != MM_FP64 && prec != MM_TF32X3) return MM_ERR_ARG;
+    if (prec != MM_FP64 && prec != MM_TF32X3 && prec != MM_BF16X3) return MM_ERR_ARG;
     int64_t N = 1;
     for (int mu = 0; mu < d; ++mu) {
         if (n[mu] < 1 || n[mu] > 8192) return MM_ERR_SHAPE;
@@ -264,7 +264,7 @@ extern "C" int phi_plan_create(mm_plan* out, int d, const int64_t* n, const doub
         extract_tridiag_kernel<<<grid_for(n[mu]), 256, 0, s>>>(p->A[mu], (int)n[mu], p->diag3[mu]);
         if (cudaGetLastError() != cudaSuccess) { rc = MM_ERR_CUDA; goto fail; }
     }
-    if (prec == MM_TF32X3) {
+    if (prec == MM_TF32X3 || prec == MM_BF16X3) {
         rc = plan_prepare_tf32(p, s);
         if (rc) goto fail;
     }

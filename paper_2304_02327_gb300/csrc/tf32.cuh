@@ -11,7 +11,7 @@ namespace mm {
 int tf32_mode_product(mm_plan_s* p, int ell, int mu, const void* in, bool in_fp64, float* out,
                       const Epi* last, cudaStream_t s);
 // MM_OK if a direction of size n is supported by the TF32x3 kernel.
-int tf32_supported(int n);
+int tf32_supported(int prec, int n);
 // Tucker chain of the mixed form: FP64 (in64) or FP32 input, FP32 intermediates
 // in F1/F2 (N floats each), FP64 epilogue `last` on the last mode (expint_mixed.cu).
 int mixed_tucker(mm_plan_s* p, int ell, const void* in, bool in64, float* F1, float* F2,

@@ -1,4 +1,7 @@
-"""Parity of the TF32x3 tensor-core form (tcgen05) with the FP64 oracle.
+"""Parity of the split-precision tensor-core forms (tcgen05) with the FP64 oracle.
+
+Both mixed forms are run by every test: TF32x3 (operand in two TF32 parts,
+Phi in three) and BF16x3 (operand and Phi in three BF16 parts each).
 
 Tolerances come from the arithmetic: operands are split x = hi + lo with
 |x - hi - lo| <= 2^-24 |x|, products drop lo*lo (<= 2^-22 |ab| relative to the
@@ -29,6 +32,9 @@ TOL_STEP = 1e-6
 TOL_LAWSON_PER_STEP = 5e-7
 
 
+FORMS = ["tf32x3", "bf16x3"]
+
+
 @pytest.fixture(scope="module")
 def api():
     if not torch.cuda.is_available():
@@ -39,6 +45,11 @@ def api():
     return _api
 
 
+@pytest.fixture(params=FORMS)
+def form(request):
+    return request.param
+
+
 def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
 
@@ -46,11 +57,11 @@ def dev(x):
 @pytest.mark.parametrize("ns", [(64,), (128, 128), (33, 17), (48, 64, 80), (320, 40, 2),
                                 (20, 17, 13), (5, 4, 3, 6), (128, 300), (1, 9, 4)])
 @pytest.mark.parametrize("ell", [0, 1, 2])
-def test_tf32_mumode_apply_matches_oracle(api, ns, ell):
+def test_mixed_mumode_apply_matches_oracle(api, form, ns, ell):
     tau = 2e-3
     As = [wl.fd_matrix(n, 0.4, 0.9) for n in ns]
     V = wl.random_tensor(tuple(reversed(ns)), seed=len(ns) * 11 + ell)
-    plan = api.Plan(As, tau, 2, "tf32x3")
+    plan = api.Plan(As, tau, 2, form)
     P = api.mumode_phi_apply(plan, ell, dev(V), alpha=1.0)
     torch.cuda.synchronize()
     assert plan.status() == 0
@@ -58,12 +69,12 @@ def test_tf32_mumode_apply_matches_oracle(api, ns, ell):
     assert rel_err_inf(P.cpu().numpy(), ref) <= TOL_APPLY
 
 
-def test_tf32_dense_random_operator(api):
+def test_mixed_dense_random_operator(api, form):
     """Dense, non-decaying matrices: error measured against sum |Phi| |V| bounds."""
     ns = (96, 80)
     As = [0.3 * wl.random_dense(n, 3 + n) for n in ns]
     V = wl.random_tensor((80, 96), 5)
-    plan = api.Plan(As, 1.0, 1, "tf32x3")
+    plan = api.Plan(As, 1.0, 1, form)
     P = api.mumode_phi_apply(plan, 1, dev(V)).cpu().numpy()
     phis = [phi_matrices(A, 1)[1] for A in As]
     ref = phisplit_apply(V, phis, 1)
@@ -81,54 +92,54 @@ def run_pair(api, p, prec):
 
 
 @pytest.mark.parametrize("scheme", [wl.EXPEULER, wl.ETD2RK, wl.LAWSON_EULER, wl.LAWSON2B])
-def test_tf32_schemes_small(api, scheme):
+def test_mixed_schemes_small(api, form, scheme):
     p = wl.adr_3d(seed=5, steps=5, scheme=scheme, sizes=(40, 33, 24))
-    got, ref = run_pair(api, p, "tf32x3")
+    got, ref = run_pair(api, p, form)
     lawson = scheme in (wl.LAWSON_EULER, wl.LAWSON2B)
     assert rel_err_inf(got, ref) <= (TOL_LAWSON_PER_STEP * p.steps if lawson else TOL_STEP)
 
 
-def test_tf32_allen_cahn_n64(api):
+def test_mixed_allen_cahn_n64(api, form):
     p = wl.workload("ac2d_n64_expeuler")
-    got, ref = run_pair(api, p, "tf32x3")
+    got, ref = run_pair(api, p, form)
     assert rel_err_inf(got, ref) <= TOL_STEP
 
 
-def test_tf32_adr3d_n128_full(api):
-    """3D ADR n = 128, 100 ETD2RK steps in the TF32x3 form against the FP64 oracle."""
+def test_mixed_adr3d_n128_full(api, form):
+    """3D ADR n = 128, 100 ETD2RK steps in the mixed form against the FP64 oracle."""
     p = wl.workload("adr3d_n128_etd2rk")
-    got, ref = run_pair(api, p, "tf32x3")
+    got, ref = run_pair(api, p, form)
     assert rel_err_inf(got, ref) <= TOL_STEP and rel_err_fro(got, ref) <= TOL_STEP
 
 
-def test_tf32_adr3d_n320_two_steps(api):
-    """3D ADR at n = 320 (N = 32.8M), two ETD2RK steps, TF32x3 vs the FP64 oracle."""
+def test_mixed_adr3d_n320_two_steps(api, form):
+    """3D ADR at n = 320 (N = 32.8M), two ETD2RK steps, mixed form vs the FP64 oracle."""
     p = wl.workload("adr3d_n320_etd2rk", steps=2)
-    got, ref = run_pair(api, p, "tf32x3")
+    got, ref = run_pair(api, p, form)
     assert rel_err_inf(got, ref) <= TOL_STEP
 
 
-def test_tf32_paper_adr_error(api):
+def test_mixed_paper_adr_error(api, form):
     """The paper's ADR test at 40x41x42, 40 ETD2RK steps: the mixed form reproduces the
     printed error 3.034138277914e-4 to the mixed tolerance."""
     p = wl.paper_adr_3d((40, 41, 42), 40, wl.ETD2RK)
-    plan, g, U = api.setup(p, "tf32x3")
+    plan, g, U = api.setup(p, form)
     api.expint_step(plan, wl.ETD2RK, U, 40, g=g)
     e = rel_err_inf(U.cpu().numpy(), np.e * p.u0)
     assert abs(e - 0.0003034138277914) <= 1e-6, e
 
 
-def test_tf32_rejects_unsupported_size(api):
+def test_mixed_rejects_unsupported_size(api, form):
     with pytest.raises(api.PhisplitError) as e:          # n > 512: beyond the TMEM columns
-        api.Plan([wl.fd_matrix(600, 0.1)], 1e-3, 1, "tf32x3")
+        api.Plan([wl.fd_matrix(600, 0.1)], 1e-3, 1, form)
     assert e.value.code == -3
 
 
-def test_tf32_large_direction_split_across_ctas(api):
-    """n = 400 runs with its output columns split over three CTAs."""
+def test_mixed_large_direction_split_across_ctas(api, form):
+    """n = 400 runs with its output columns split over several CTAs."""
     As = [wl.fd_matrix(400, 0.3, 0.5), wl.fd_matrix(24, 0.2)]
     V = wl.random_tensor((24, 400), 9)
-    plan = api.Plan(As, 1e-3, 1, "tf32x3")
+    plan = api.Plan(As, 1e-3, 1, form)
     P = api.mumode_phi_apply(plan, 1, dev(V)).cpu().numpy()
     ref = phisplit_apply(V, [phi_matrices(1e-3 * A, 1)[1] for A in As], 1)
     assert rel_err_inf(P, ref) <= TOL_APPLY
