@@ -34,7 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2304_02327_gb300 import workloads as wl  # noqa: E402
+from paper_2304_02327_gb300 import parallel, workloads as wl  # noqa: E402
 
 METRIC = "DOF-steps/s"
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2, written between timed steps
@@ -243,12 +243,8 @@ def ours(args):
                                               api.KC_PREPASS, api.KC_SPLIT)}
     api.trace_enable(False)
     assert plan.status() == 0, "non-finite state during the timed steps"
-    t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * N * args.steps / (t_ms / 1e3)
+    t_ms = parallel.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device="cuda")
+    value = parallel.job_throughput([N * args.steps] * world, t_ms / 1e3)
 
     # ---- e2e: pinned host state in, one step, state out, every step ----
     U_host = torch.from_numpy(np.ascontiguousarray(p.u0)).pin_memory()
@@ -265,12 +261,8 @@ def ours(args):
         U_host.copy_(U_dev, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
-    e2e_value = world * N * e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = parallel.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    e2e_value = parallel.job_throughput([N * e2e_steps] * world, e2e_ms / 1e3)
 
     if rank != 0:
         if world > 1:

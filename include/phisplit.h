@@ -29,9 +29,13 @@
  *   written by an integrator step, a bounded wait that ran out) are OR-ed into a
  *   per-plan status word that phi_plan_status reads.
  * - Precision.  MM_FP64: every product and sum in double (the plain form).
- *   MM_TF32X3: the mu-mode products run on tcgen05 tensor cores with operands
- *   split x = hi + lo into TF32 parts and hi*hi + hi*lo + lo*hi accumulated in
- *   FP32; phi matrices, K u + g and the state update stay FP64.
+ *   MM_TF32X3 / MM_BF16X3: the mu-mode products run on tcgen05 tensor cores with
+ *   split operands accumulated in FP32 (TF32x3: operand in two TF32 parts, phi in
+ *   three, 4 products; BF16x3: both in three BF16 parts, 6 products); the phi
+ *   matrices are formed in FP64 and the state update u + tau*y is FP64, while
+ *   K u + g and the Tucker intermediates are FP32.  The tensor cores' FP32
+ *   accumulation truncates toward zero, which leaves a one-sided relative error of
+ *   order 1e-7 * n/128 per Tucker apply (BF16x3 about half of TF32x3).
  */
 #ifndef PHISPLIT_H
 #define PHISPLIT_H
