@@ -62,7 +62,11 @@ struct Epi {
     double* U;
     double* U2;
     double* W2;
-    float* W2f;         // mixed form: FP32 stage-2 input g(U2) - g(U)
+    float* W2f;         // (unused by the current forms)
+    uint8_t* W2p;       // mixed form: parts of the stage-2 input g(U2) - g(U), mode-1 layout
+    int64_t w2_pitch;   //   elements per part
+    int w2_n, w2_p;     //   fibre length and row pitch of the mode-1 layout
+    int prec;           //   the plan's precision form
     double t0, t1;
     PointwiseG g;
     unsigned int* status;

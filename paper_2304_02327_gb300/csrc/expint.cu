@@ -162,6 +162,7 @@ using namespace mm;
 
 extern "C" size_t mumode_workspace_bytes(mm_plan p) {
     if (!p) return 0;
+    if (p->prec != MM_FP64) return mixed_mumode_workspace_bytes(p);
     return p->d >= 2 ? (size_t)p->N * sizeof(double) : 0;
 }
 
@@ -171,7 +172,9 @@ extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, 
     const size_t bytes = (size_t)p->N * sizeof(double);
     if (overlaps(V, bytes, P, bytes)) return MM_ERR_ARG;
     const size_t need = mumode_workspace_bytes(p);
-    if (need && (!ws || ws_bytes < need || ((uintptr_t)ws & 7))) return MM_ERR_WORKSPACE;
+    // the mixed forms address their operand buffers with TMA: 16-byte alignment
+    const uintptr_t amask = p->prec == MM_FP64 ? 7 : 15;
+    if (need && (!ws || ws_bytes < need || ((uintptr_t)ws & amask))) return MM_ERR_WORKSPACE;
     if (need && (overlaps(ws, need, V, bytes) || overlaps(ws, need, P, bytes))) return MM_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     double* T = (double*)ws;
@@ -179,7 +182,14 @@ extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, 
     last.kind = EPI_STORE;
     last.alpha = alpha * pow(factorial(ell), p->d - 1);
     last.C = P;
-    if (p->prec != MM_FP64) return mixed_tucker(p, ell, V, true, (float*)T, (float*)T + p->N, last, s);
+    if (p->prec != MM_FP64) {
+        // split V into the mode-1 operand parts, then the tensor-core chain
+        const size_t S = part_set_bytes(p);
+        uint8_t* w = (uint8_t*)ws;
+        int rc = mixed_split_input(p, V, w, s);
+        if (rc) return rc;
+        return mixed_tucker(p, ell, w, w + S, w + 2 * S, (float*)(w + 3 * S), last, s);
+    }
     double* outs[MM_MAX_D];
     // mode d writes P; mode d-1 writes T; earlier modes alternate backwards
     for (int k = 0; k < p->d - 1; ++k) outs[k] = ((p->d - 2 - k) % 2 == 0) ? T : P;
@@ -188,6 +198,7 @@ extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, 
 
 extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g) {
     if (!p) return 0;
+    if (p->prec != MM_FP64) return mixed_workspace_bytes(p, scheme);
     const size_t N = (size_t)p->N;
     size_t buffers = 2;                          // Tucker ping-pong X, Y
     if (scheme == MM_ETD2RK) buffers = 3;        // + U2
@@ -214,7 +225,8 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     }
     if (gk == MM_G_ADR_MANUFACTURED && (!g->psi_a || !g->psi_b)) return MM_ERR_ARG;
     const size_t need = expint_workspace_bytes(p, scheme, g);
-    if (!ws || ws_bytes < need || ((uintptr_t)ws & 7)) return MM_ERR_WORKSPACE;
+    const uintptr_t amask = p->prec == MM_FP64 ? 7 : 15;
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & amask)) return MM_ERR_WORKSPACE;
     const size_t bytes = (size_t)p->N * sizeof(double);
     if (overlaps(ws, need, U, bytes)) return MM_ERR_ARG;
     if (nsteps == 0) return MM_OK;
@@ -222,7 +234,7 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     cudaStream_t s = (cudaStream_t)stream;
     if (p->prec != MM_FP64) {
         if (gk == MM_G_RICCATI) return MM_ERR_UNSUPPORTED;
-        return mixed_expint(p, scheme, pointwise_of(g), U, t0, nsteps, (double*)ws, s);
+        return mixed_expint(p, scheme, pointwise_of(g), U, t0, nsteps, (uint8_t*)ws, s);
     }
     const int64_t N = p->N;
     double* X = (double*)ws;

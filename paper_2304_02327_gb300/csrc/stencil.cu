@@ -13,7 +13,10 @@
 #include "common.cuh"
 #include "stencil.cuh"
 #include "trace.cuh"
+#include "forms.cuh"
 #include "mixed.cuh"
+
+#include <algorithm>
 
 namespace mm {
 
@@ -53,43 +56,59 @@ __global__ void __launch_bounds__(256) prepass_kernel(StencilArgs a) {
     }
 }
 
+// U -> (hi, lo) FP32 pairs, exact to 2^-46, one conversion per element.
+__global__ void __launch_bounds__(256) split_pairs_kernel(const double* __restrict__ U,
+                                                           float2* __restrict__ P, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float h, l;
+        mx::d2ff(__ldg(U + i), h, l);
+        P[i] = make_float2(h, l);
+    }
+}
+
+// One thread per element (flat index, i_1 fastest); the neighbours' pairs come
+// from L1/L2, differences are taken pairwise so they keep their own accuracy.
 __global__ void __launch_bounds__(256) prepass_mixed_kernel(StencilArgsMixed a) {
-    const int64_t rows = a.N / a.n[0];
-    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
-        int idx[MM_MAX_D];
-        int64_t rem = row;
-        for (int mu = 1; mu < a.d; ++mu) { idx[mu] = (int)(rem % a.n[mu]); rem /= a.n[mu]; }
-        const int64_t base = row * a.n[0];
-        for (int i1 = threadIdx.x; i1 < a.n[0]; i1 += blockDim.x) {
-            const int64_t off = base + i1;
-            float uh, ul;
-            mx::d2ff(a.U[off], uh, ul);
-            const float u = uh + ul;
-            const float g = mx::g32(a.g, u, a.t, off);
-            if (a.mode == PRE_KU_G) {
-                float acc = g;
-                idx[0] = i1;
-                for (int mu = 0; mu < a.d; ++mu) {
-                    const int i = idx[mu];
-                    const int nm = (int)a.n[mu];
-                    const float* cf = a.coef[mu];
-                    acc = fmaf(cf[2 * nm + i], u, acc);
-                    if (i > 0) {
-                        float vh, vl;
-                        mx::d2ff(a.U[off - a.stride[mu]], vh, vl);
-                        acc = fmaf(cf[i], (vh - uh) + (vl - ul), acc);
-                    }
-                    if (i + 1 < nm) {
-                        float vh, vl;
-                        mx::d2ff(a.U[off + a.stride[mu]], vh, vl);
-                        acc = fmaf(cf[nm + i], (vh - uh) + (vl - ul), acc);
-                    }
+    for (int64_t off = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; off < a.N;
+         off += (int64_t)gridDim.x * blockDim.x) {
+        float uh, ul;
+        if (a.mode == PRE_KU_G) {
+            const float2 pu = __ldg(a.Up + off);
+            uh = pu.x; ul = pu.y;
+        } else {
+            mx::d2ff(__ldg(a.U + off), uh, ul);
+        }
+        const float u = uh + ul;
+        const float g = mx::g32(a.g, u, a.t, off);
+        if (a.mode == PRE_KU_G) {
+            float acc = g;
+            const bool small = a.N < (int64_t(1) << 31);
+            int64_t rem = off;
+            uint32_t rem32 = (uint32_t)off;
+            for (int mu = 0; mu < a.d; ++mu) {
+                const int nm = (int)a.n[mu];
+                int i;
+                if (small) { i = (int)(rem32 % (uint32_t)nm); rem32 /= (uint32_t)nm; }
+                else { i = (int)(rem % nm); rem /= nm; }
+                const float* cf = a.coef[mu];
+                acc = fmaf(cf[2 * nm + i], u, acc);
+                if (i > 0) {
+                    const float2 v = __ldg(a.Up + off - a.stride[mu]);
+                    acc = fmaf(cf[i], (v.x - uh) + (v.y - ul), acc);
                 }
-                a.Wf[off] = acc;
-            } else {
-                a.Wf[off] = fmaf(a.ca, g, uh) + ul;
-                if (a.W2f) a.W2f[off] = fmaf(a.cb, g, uh) + ul;
+                if (i + 1 < nm) {
+                    const float2 v = __ldg(a.Up + off + a.stride[mu]);
+                    acc = fmaf(cf[nm + i], (v.x - uh) + (v.y - ul), acc);
+                }
             }
+            const int64_t pos = (off % a.n[0]) + (int64_t)a.p1 * (off / a.n[0]);
+            store_parts_prec(a.prec, a.Wp, a.part_pitch, pos, acc, 0.f);
+        } else {
+            // u + c g as (uh + c g) + ul: the low part of u enters the split exactly
+            const int64_t pos = (off % a.n[0]) + (int64_t)a.p1 * (off / a.n[0]);
+            store_parts_prec(a.prec, a.Wp, a.part_pitch, pos, fmaf(a.ca, g, uh), ul);
+            if (a.W2p) store_parts_prec(a.prec, a.W2p, a.part_pitch, pos, fmaf(a.cb, g, uh), ul);
         }
     }
 }
@@ -107,12 +126,17 @@ __global__ void stencil_coef_kernel(const double* __restrict__ A, int n, float* 
 
 }  // namespace
 
-int launch_prepass_mixed(const StencilArgsMixed& a, cudaStream_t s) {
-    const int64_t rows = a.N / a.n[0];
-    int64_t grid = rows < 65535LL * 16 ? rows : 65535LL * 16;
-    int block = a.n[0] >= 256 ? 256 : (a.n[0] >= 128 ? 128 : (a.n[0] >= 64 ? 64 : 32));
+int launch_prepass_mixed(const StencilArgsMixed& a0, float2* Up, cudaStream_t s) {
+    const int64_t blocks = std::min<int64_t>((a0.N + 255) / 256, (int64_t)num_sms() * 16);
+    StencilArgsMixed a = a0;
+    if (a.mode == PRE_KU_G) {
+        TraceScope tr(KC_SPLIT, s);
+        split_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.U, Up, a.N);
+        MM_LAUNCH_CHECK();
+        a.Up = Up;
+    }
     TraceScope tr(KC_PREPASS, s);
-    prepass_mixed_kernel<<<(unsigned)grid, block, 0, s>>>(a);
+    prepass_mixed_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
     MM_LAUNCH_CHECK();
     return MM_OK;
 }

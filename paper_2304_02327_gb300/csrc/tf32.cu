@@ -1,36 +1,43 @@
-// TF32x3 mu-mode contraction on tcgen05 tensor cores (sm_103a).
+// Split-precision mu-mode contraction on tcgen05 tensor cores (sm_103a), fed by TMA.
 //
-// One mode product Y[l, i, r] = sum_j Phi[i, j] V[l, j, r] is a GEMM whose rows are
-// the fibres of V along direction mu: row q = (l, r) with l = q mod L, r = q div L,
-// fibre element j at V[l + L j + L n r].  Flattening the rows this way makes every
-// mode -- the contiguous first, the strided middle and the last -- the same
-// 128-row-tile GEMM with no ragged middle tiles and no transpose pass:
+// Mode rotation.  Mode mu reads its operand with the contraction index i_mu
+// fastest -- fibre ("row") q holds its n_mu values contiguously, rows at a pitch
+// p_mu >= n_mu -- and writes its output with the new index i_mu' slowest, in the
+// layout the next mode reads: output element (q, i) goes to fibre position
+// q mod n_{mu+1} of row q div n_{mu+1} + (R_mu / n_{mu+1}) i.  After d modes the
+// order is back to natural (i_1 fastest), so no mode ever reads a strided operand
+// and there is no transpose pass: every mode is the same K-major GEMM
 //
-//   MMA M = 128 rows (TMEM lanes), MMA N = Nc output columns i (all n of them, or
-//   half when n > 256), K = n inputs j in blocks of 32 (one 128-byte swizzle row).
+//   M = 128 rows (TMEM lanes) per tile, N = nc output columns i (<= 128 per CTA),
+//   K = n_mu in blocks of one 128-byte swizzle row (32 TF32 or 64 BF16 values).
 //
-// Split precision: the tensor operand is x = x_hi + x_lo with x_hi = rn_tf32(x),
-// x_lo = rn_tf32(x - x_hi) (residual <= 2^-22 |x|, a different pattern every
-// step); the fixed matrix is split three ways, Phi = b0 + b1 + b2 (residual
-// 2^-33), because its rounding error would otherwise repeat identically every
-// step and grow linearly over a run.  The products x_hi*b0 go to G accumulators,
-// one per contiguous group of K-blocks, and the corrections x_lo*b0 + x_hi*b1 +
-// x_hi*b2 to one more; the epilogue adds the G + 1 FP32 partial sums.  Keeping
-// the small corrections out of the main sum and restarting it every few K-blocks
-// cuts the number of roundings of a full-magnitude FP32 sum per output from
-// 4n/8 to about n/(8G), which is what bounds a long FP32 accumulation.
+// Split precision.  The operand is stored already split into parts by whoever
+// wrote it (the prepass, the previous mode's epilogue, the update pass):
+//   TF32x3: x = a0 + a1 (TF32, residual 2^-22), Phi = b0 + b1 + b2, 4 MMAs
+//           a0 b0 | a1 b0 + a0 b1 + a0 b2
+//   BF16x3: x = a0 + a1 + a2 (BF16, residual ~2^-25), Phi in 3 parts, 6 MMAs
+//           a0 b0 | a1 b0 + a0 b1 + a2 b0 + a1 b1 + a0 b2
+// The main product goes to one TMEM accumulator and the corrections to a
+// companion one, added in FP32 by the epilogue, so the small terms never round a
+// full-magnitude sum.  The three-way split of the fixed matrix keeps its rounding,
+// which would repeat identically every step, at 2^-33.
 //
-// The Phi operand is split once by the plan into the exact shared-memory image
-// the MMA reads and streamed per K-block with bulk async copies (the TMA engine).
-// The V operand is loaded by four producer warps a K-block ahead into registers
-// (coalesced: along rows for strided modes, along the fibre for the contiguous
-// one), split, and stored K-major with the 128-byte swizzle.  One thread issues
-// the MMAs; all eight warps then drain TMEM and either store FP32 (intermediate
-// modes) or run the FP64 integrator epilogue (last mode).
+// Kernel structure: persistent, one CTA per SM over tiles t = blockIdx.x + i grid.
+//   warp 0      loader: per K-block, one TMA tensor load per operand part (the
+//               3-D map {K, rows, part} zero-fills the ragged K tail and the last
+//               rows) and bulk copies of this tile's columns of the plan's Phi image
+//   warp 1      MMA issuer (one thread), accumulator sets alternate between tiles
+//   warps 2-5   epilogue: drain TMEM (two sets: the epilogue of tile i overlaps the
+//               MMAs of tile i + 1), split the FP32 result into the next mode's
+//               parts (or write FP32 after the last mode)
+// Every mbarrier wait is bounded (tcgen05.cuh).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
+#include "forms.cuh"
 #include "mixed.cuh"
 #include "plan.cuh"
 #include "stencil.cuh"
@@ -42,33 +49,14 @@ namespace mm {
 
 namespace {
 
-constexpr int kRows = 128;                 // MMA M / rows per CTA tile
-constexpr uint32_t kATile = kRows * 128;   // bytes of one A tile part (128 B rows)
+constexpr int kRows = 128;                 // MMA M / rows per tile
+constexpr uint32_t kATile = kRows * 128;   // bytes of one operand part tile (128-byte rows)
 constexpr int kMaxStages = 4;
-constexpr int kMaxGroups = 4;
 constexpr int kBParts = 3;                 // Phi = b0 + b1 + b2 in both forms
+constexpr int kNcMax = 128;                // two sets of [main | corr] fit 512 TMEM columns
+constexpr int kBars = 2 * kMaxStages + 5;  // full, empty per stage; acc_full/empty x2; mma_done
 constexpr int kSmemLimit = 227 * 1024;
-
-// The two split-precision forms.  A K-block is one 128-byte swizzle row of
-// operand elements; every MMA consumes 32 bytes of K (8 TF32 or 16 BF16).
-//   TF32x3: x = a0 + a1 (TF32, residual 2^-22), Phi 3 parts, products
-//           a0 b0 | a1 b0 + a0 b1 + a0 b2                          (4 MMAs)
-//   BF16x3: x = a0 + a1 + a2 (BF16, residual ~2^-25), Phi 3 parts, products
-//           a0 b0 | a1 b0 + a0 b1 + a2 b0 + a1 b1 + a0 b2          (6 MMAs)
-// The main product a0 b0 goes to the K-grouped accumulators, the rest to one
-// correction accumulator.
-struct FormTF32 {
-    static constexpr int kElem = 4, kBK = 32, kAParts = 2, kNcMax = 192;
-    static constexpr int kCorr = 3;
-    __host__ __device__ static constexpr int corr_a(int c) { return c == 0 ? 1 : 0; }
-    __host__ __device__ static constexpr int corr_b(int c) { return c == 0 ? 0 : c; }
-};
-struct FormBF16 {
-    static constexpr int kElem = 2, kBK = 64, kAParts = 3, kNcMax = 160;
-    static constexpr int kCorr = 5;
-    __host__ __device__ static constexpr int corr_a(int c) { return c == 0 ? 1 : c == 2 ? 2 : c == 3 ? 1 : 0; }
-    __host__ __device__ static constexpr int corr_b(int c) { return c == 1 ? 1 : c == 3 ? 1 : c == 4 ? 2 : 0; }
-};
+constexpr int kThreads = 192;
 
 template <class F> __device__ __forceinline__ uint32_t idesc_of(int nc);
 template <> __device__ __forceinline__ uint32_t idesc_of<FormTF32>(int nc) { return tc::idesc_tf32(128, nc); }
@@ -90,203 +78,65 @@ __host__ __device__ __forceinline__ uint32_t sw_off(uint32_t row, uint32_t k) {
            (k % per) * F::kElem;
 }
 
-struct Tf32Mode {
-    int n, n_pad, nkb, nc, splits, groups, stages;   // n_pad: image rows per half (splits * nc)
-    int64_t L, rows;
-    const void* in;
-    float* out;
+struct TcMode {
+    int n, nkb, nc, splits, stages, n_img;
+    int64_t rows, row_tiles;
     const uint8_t* bimg;
-    uint32_t tmem_cols;
+    // output: next mode's parts (layout above) or FP32 after the last mode
+    int last;
+    float* yout;
+    uint8_t* pout;           // part q at pout + q * out_part_pitch elements
+    int64_t out_part_pitch;  // elements per part
+    int next_n, next_p;      // next mode's fibre length and row pitch
+    int64_t next_rows_per_i; // R_mu / n_{mu+1}
     unsigned int* status;
 };
 
-// Split one operand value into the form's parts, as 32-bit patterns (TF32 in an
-// FP32 container) or 16-bit patterns (BF16) in the low half.
-template <class F> __device__ __forceinline__ void split_parts(float x, float xl, uint32_t (&p)[3]);
-template <> __device__ __forceinline__ void split_parts<FormTF32>(float x, float xl, uint32_t (&p)[3]) {
-    const float h = mx::tf32(x);
-    const float l = mx::tf32((x - h) + xl);
-    p[0] = __float_as_uint(h); p[1] = __float_as_uint(l); p[2] = 0;
-}
-template <> __device__ __forceinline__ void split_parts<FormBF16>(float x, float xl, uint32_t (&p)[3]) {
-    const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
-    const float r1 = (x - __bfloat162float(b0)) + xl;
-    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(b1);
-    const __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
-    p[0] = __bfloat16_as_ushort(b0); p[1] = __bfloat16_as_ushort(b1); p[2] = __bfloat16_as_ushort(b2);
-}
-template <class F> __device__ __forceinline__ void split_val(float x, uint32_t (&p)[3]) { split_parts<F>(x, 0.f, p); }
-template <class F> __device__ __forceinline__ void split_val(double x, uint32_t (&p)[3]) {
-    float a, b;
-    mx::d2ff(x, a, b);
-    split_parts<F>(a, b, p);
+// 3-D TMA load of one part tile: box {K block, 128 rows} at (k0, row0, part).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int k0, int row0, int part,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(map), "r"(k0), "r"(row0), "r"(part), "r"(bar)
+        : "memory");
 }
 
-__device__ __forceinline__ void flag_nonfinite_bits(const Epi& e, double v) {
-    if (!mx::finite_bits(v) && e.status) atomicOr(e.status, MM_STATUS_NONFINITE);
-}
 
-// Last-mode epilogue of the mixed form, 16 consecutive output columns of one
-// row: the state update in FP64 (one DFMA per element), everything else in FP32.
-// The state values are loaded into registers first, so the loads are not
-// serialised behind the stores.
-__device__ __forceinline__ void mixed_epilogue16(const Epi& e, const float (&y)[16], int64_t base,
-                                                 int i0, int n, int64_t L, float alphaf, float t0f,
-                                                 float t1f) {
-    if (e.kind == EPI_STORE) {
-#pragma unroll
-        for (int t = 0; t < 16; ++t)
-            if (i0 + t < n) e.C[base + (int64_t)(i0 + t) * L] = e.alpha * mx::f2d(y[t]);
-        return;
-    }
-    const double* src = (e.kind == EPI_EE || e.kind == EPI_ETD_S1) ? e.U : e.U2;
-    double u[16];
-#pragma unroll
-    for (int t = 0; t < 16; ++t) u[t] = (i0 + t < n) ? __ldg(src + base + (int64_t)(i0 + t) * L) : 0.0;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) {
-        if (i0 + t >= n) continue;
-        const int64_t off = base + (int64_t)(i0 + t) * L;
-        switch (e.kind) {
-        case EPI_EE:
-        case EPI_ETD_S2: {
-            const double v = fma(e.alpha, mx::f2d(y[t]), u[t]);
-            flag_nonfinite_bits(e, v);
-            e.U[off] = v;
-            break;
-        }
-        case EPI_ETD_S1: {
-            e.U2[off] = fma(e.alpha, mx::f2d(y[t]), u[t]);
-            float uh, ul;
-            mx::d2ff(u[t], uh, ul);
-            e.W2f[off] = mx::dg32(e.g, uh + ul, alphaf * y[t], t0f, t1f, off);
-            break;
-        }
-        case EPI_LAWSON2: {
-            float uh, ul;
-            mx::d2ff(u[t], uh, ul);
-            const float gv = (float)e.beta * mx::g32(e.g, uh + ul, t1f, off);
-            const double v = fma(e.alpha, mx::f2d(y[t]), mx::f2d(gv));
-            flag_nonfinite_bits(e, v);
-            e.U[off] = v;
-            break;
-        }
-        default: break;
-        }
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
-
-// The producer's register stage: one K-block slice of the A operand (kBK values
-// per row of the 128-row tile).
-//   strided modes (L > 1): thread r owns row r, values along j (each load
-//     instruction of a warp covers 32 consecutive rows: coalesced);
-//   contiguous mode (L == 1): thread t owns runs of 8 consecutive j of several
-//     rows, so each load instruction covers whole row segments.
-template <class F, typename TIn>
-struct AStage {
-    static constexpr int kVals = F::kBK;            // values per thread per K-block
-    static constexpr int kRun = 8;                   // contiguous-mode run length
-    static constexpr int kRunsPerRow = F::kBK / kRun;
-    static constexpr int kRowStep = 128 / kRunsPerRow;
-    TIn v[kVals];
-
-    __device__ __forceinline__ void load(const Tf32Mode& a, const TIn* __restrict__ in, int64_t q0,
-                                         int kb, int tid) {
-        const int j0 = kb * F::kBK;
-        if (a.L > 1) {
-            const int64_t q = q0 + tid;
-            const bool valid = q < a.rows;
-            const int64_t base = valid ? (q % a.L) + (q / a.L) * a.L * a.n : 0;
-#pragma unroll
-            for (int t = 0; t < kVals; ++t) {
-                const int j = j0 + t;
-                v[t] = (valid && j < a.n) ? __ldg(in + base + (int64_t)j * a.L) : (TIn)0;
-            }
-        } else {
-            const int c = tid % kRunsPerRow, rg = tid / kRunsPerRow;
-#pragma unroll
-            for (int i = 0; i < kVals / kRun; ++i) {
-                const int64_t q = q0 + rg + kRowStep * i;
-                const int j = j0 + c * kRun;
-#pragma unroll
-                for (int e = 0; e < kRun; ++e)
-                    v[i * kRun + e] = (q < a.rows && j + e < a.n) ? __ldg(in + q * a.n + j + e) : (TIn)0;
-            }
-        }
-    }
-
-    // Split and store: each 16-byte chunk of every part is written at once.
-    __device__ __forceinline__ void store(const Tf32Mode& a, uint8_t* const (&parts)[3], int tid) const {
-        constexpr int per = 16 / F::kElem;               // elements per 16-byte chunk
-        if (a.L > 1) {
-#pragma unroll
-            for (int c = 0; c < kVals / per; ++c) store_chunk(parts, tid, c * per, &v[c * per]);
-        } else {
-            const int c = tid % kRunsPerRow, rg = tid / kRunsPerRow;
-#pragma unroll
-            for (int i = 0; i < kVals / kRun; ++i)
-#pragma unroll
-                for (int h = 0; h < kRun / per; ++h)
-                    store_chunk(parts, rg + kRowStep * i, c * kRun + h * per, &v[i * kRun + h * per]);
-        }
-    }
-
-    __device__ __forceinline__ static void store_chunk(uint8_t* const (&parts)[3], int row, int k0,
-                                                       const TIn* x) {
-        constexpr int per = 16 / F::kElem;
-        uint32_t w[3][4] = {};
-#pragma unroll
-        for (int e = 0; e < per; ++e) {
-            uint32_t pp[3];
-            split_val<F>(x[e], pp);
-#pragma unroll
-            for (int q = 0; q < F::kAParts; ++q) {
-                if (F::kElem == 4) w[q][e] = pp[q];
-                else w[q][e >> 1] |= pp[q] << (16 * (e & 1));
-            }
-        }
-        const uint32_t off = sw_off<F>(row, k0);
-#pragma unroll
-        for (int q = 0; q < F::kAParts; ++q)
-            *(uint4*)(parts[q] + off) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
-    }
-};
-
-template <class F, typename TIn, bool LAST>
-__global__ void __launch_bounds__(256, 1) tc_mode_kernel(Tf32Mode a, Epi e) {
+template <class F>
+__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __grid_constant__ CUtensorMap amap) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t b_tile = (uint32_t)a.nc * 128u;
     const uint32_t a_bytes = F::kAParts * kATile;
     const uint32_t stage_bytes = a_bytes + kBParts * b_tile;
     uint64_t* bars = (uint64_t*)(smem + a.stages * stage_bytes);
-    uint32_t* tmem_slot = (uint32_t*)(bars + 3 * kMaxStages + 1);
+    uint32_t* tmem_slot = (uint32_t*)(bars + kBars);
     auto full = [&](int s) { return tc::smem_u32(bars + s); };
-    auto bfull = [&](int s) { return tc::smem_u32(bars + kMaxStages + s); };
-    auto empty = [&](int s) { return tc::smem_u32(bars + 2 * kMaxStages + s); };
-    const uint32_t accum = tc::smem_u32(bars + 3 * kMaxStages);
+    auto empty = [&](int s) { return tc::smem_u32(bars + kMaxStages + s); };
+    auto acc_full = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + b); };
+    auto acc_empty = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 2 + b); };
+    const uint32_t mma_done = tc::smem_u32(bars + 2 * kMaxStages + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int h = (int)(blockIdx.x % a.splits);                 // column slice of this CTA
-    const int64_t q0 = (int64_t)(blockIdx.x / a.splits) * kRows;
-    const int col0 = h * a.nc;                                   // first output column i
     const int stages = a.stages;
+    const int64_t ntiles = a.row_tiles * a.splits;
+    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
-            tc::mbar_init(full(s), 128);
-            tc::mbar_init(bfull(s), 1);
+            tc::mbar_init(full(s), 1);
             tc::mbar_init(empty(s), 1);
         }
-        tc::mbar_init(accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(acc_full(b), 1);
+            tc::mbar_init(acc_empty(b), 4);
+        }
+        tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) {
-        tc::tmem_alloc(tc::smem_u32(tmem_slot), a.tmem_cols);
+        tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
@@ -294,130 +144,125 @@ __global__ void __launch_bounds__(256, 1) tc_mode_kernel(Tf32Mode a, Epi e) {
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp < 4) {
-        // ---- producers: K-block kb+1 is in flight while kb is split and stored ----
-        const int tid = threadIdx.x;
-        const TIn* __restrict__ in = (const TIn*)a.in;
-        AStage<F, TIn> st;
-        st.load(a, in, q0, 0, tid);
-        for (int kb = 0; kb < a.nkb; ++kb) {
-            const int s = kb % stages;
-            if (kb >= stages && !tc::mbar_wait(empty(s), ((kb / stages) - 1) & 1, a.status)) break;
-            uint8_t* base = smem + s * stage_bytes;
-            uint8_t* const parts[3] = {base, base + kATile, base + 2 * kATile};
-            st.store(a, parts, tid);
-            tc::fence_proxy_async_smem();
-            tc::mbar_arrive(full(s));
-            if (kb + 1 < a.nkb) st.load(a, in, q0, kb + 1, tid);
-        }
-    } else if (warp == 4) {
+    if (warp == 0) {
         if (lane == 0) {
-            // ---- Phi loader: this CTA's rows of the plan's pre-split image ----
-            int issued_last[kMaxStages];
+            // ---- loader: operand parts by TMA, Phi columns by bulk copy ----
+            int64_t issued_last[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) issued_last[s] = -1;
-            const size_t kb_bytes = (size_t)kBParts * a.n_pad * 128;   // one K-block of the image
-            for (int kb = 0; kb < a.nkb; ++kb) {
-                const int s = kb % stages;
-                if (kb >= stages && !tc::mbar_wait(empty(s), ((kb / stages) - 1) & 1, a.status)) break;
-                tc::mbar_arrive_expect_tx(bfull(s), kBParts * b_tile);
-                const uint32_t dst = tc::smem_u32(smem + s * stage_bytes + a_bytes);
+            const size_t kb_bytes = (size_t)kBParts * a.n_img * 128;   // one K-block of the image
+            const int64_t total = my_tiles * a.nkb;
+            for (int64_t it = 0; it < total; ++it) {
+                const int s = (int)(it % stages);
+                if (it >= stages && !tc::mbar_wait(empty(s), (uint32_t)((it / stages) - 1) & 1, a.status)) break;
+                const int64_t t = blockIdx.x + (it / a.nkb) * gridDim.x;
+                const int kb = (int)(it % a.nkb);
+                const int row0 = (int)((t / a.splits) * kRows);
+                const int col0 = (int)(t % a.splits) * a.nc;
+                tc::mbar_arrive_expect_tx(full(s), a_bytes + kBParts * b_tile);
+                const uint32_t st = tc::smem_u32(smem + s * stage_bytes);
+                for (int q = 0; q < F::kAParts; ++q)
+                    tma_load_3d(st + q * kATile, &amap, kb * F::kBK, row0, q, full(s));
                 for (int part = 0; part < kBParts; ++part) {  // b0 rows, b1 rows, b2 rows
                     const uint8_t* src = a.bimg + (size_t)kb * kb_bytes +
-                                         (size_t)part * a.n_pad * 128 + (size_t)col0 * 128;
-                    const uint32_t d0 = dst + part * b_tile;
+                                         (size_t)part * a.n_img * 128 + (size_t)col0 * 128;
+                    const uint32_t d0 = st + a_bytes + part * b_tile;
                     for (uint32_t off = 0; off < b_tile; off += 16384) {
                         const uint32_t len = min(16384u, b_tile - off);
-                        tc::bulk_g2s(d0 + off, src + off, len, bfull(s));
+                        tc::bulk_g2s(d0 + off, src + off, len, full(s));
                     }
                 }
-                issued_last[s] = kb;
+                issued_last[s] = it;
             }
             // never leave the CTA with copies in flight
             for (int s = 0; s < stages; ++s)
-                if (issued_last[s] >= 0) tc::mbar_wait(bfull(s), (issued_last[s] / stages) & 1, a.status);
+                if (issued_last[s] >= 0)
+                    tc::mbar_wait(full(s), (uint32_t)(issued_last[s] / stages) & 1, a.status);
         }
-    } else if (warp == 5) {
+    } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer: a0 b0 into accumulator group g, corrections into the last ----
-            bool started[kMaxGroups] = {false, false, false, false};
-            const uint32_t corr = tmem + (uint32_t)(a.groups * a.nc);
+            // ---- MMA issuer ----
             const uint32_t id = idesc_of<F>(a.nc);
-            for (int kb = 0; kb < a.nkb; ++kb) {
-                const int s = kb % stages;
-                const uint32_t par = (kb / stages) & 1;
-                if (!tc::mbar_wait(full(s), par, a.status) || !tc::mbar_wait(bfull(s), par, a.status)) break;
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t i = 0; i < my_tiles && ok; ++i) {
+                const int b = (int)(i & 1);
+                if (i >= 2 && !tc::mbar_wait(acc_empty(b), (uint32_t)((i >> 1) - 1) & 1, a.status)) break;
                 tc::tc_fence_after();
-                const int g = kb * a.groups / a.nkb;
-                const uint32_t mainacc = tmem + (uint32_t)(g * a.nc);
-                const uint32_t abase = tc::smem_u32(smem + s * stage_bytes);
-                const uint32_t bbase = abase + a_bytes;
+                const uint32_t mainacc = tmem + (uint32_t)(b * 2 * a.nc);
+                const uint32_t corr = mainacc + (uint32_t)a.nc;
+                for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                    const int s = (int)(it % stages);
+                    if (!tc::mbar_wait(full(s), (uint32_t)(it / stages) & 1, a.status)) { ok = false; break; }
+                    tc::tc_fence_after();
+                    const uint32_t abase = tc::smem_u32(smem + s * stage_bytes);
+                    const uint32_t bbase = abase + a_bytes;
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t ko = kk * 32;
-                    mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), id,
-                           started[g] ? 1u : 0u);
-                    started[g] = true;
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t ko = kk * 32;
+                        const uint32_t acc = (kb | kk) != 0;
+                        mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), id, acc);
 #pragma unroll
-                    for (int c = 0; c < F::kCorr; ++c)
-                        mma<F>(corr, tc::desc_k_sw128(abase + F::corr_a(c) * kATile + ko),
-                               tc::desc_k_sw128(bbase + F::corr_b(c) * b_tile + ko), id,
-                               (c == 0 && (kb | kk) == 0) ? 0u : 1u);
+                        for (int c = 0; c < F::kCorr; ++c)
+                            mma<F>(corr, tc::desc_k_sw128(abase + F::corr_a(c) * kATile + ko),
+                                   tc::desc_k_sw128(bbase + F::corr_b(c) * b_tile + ko), id,
+                                   c == 0 ? acc : 1u);
+                    }
+                    tc::mma_commit(empty(s));
                 }
-                tc::mma_commit(empty(s));
+                if (ok) tc::mma_commit(acc_full(b));
             }
-            tc::mma_commit(accum);     // arrives once every issued MMA has completed
+            // every issued MMA has completed before TMEM can be released
+            tc::mma_commit(mma_done);
+            tc::mbar_wait(mma_done, 0, a.status);
+        }
+    } else {
+        // ---- epilogue: lane quarter (warp mod 4), one row per thread ----
+        const int quarter = warp & 3;
+        const int r = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        for (int64_t i = 0; i < my_tiles; ++i) {
+            const int b = (int)(i & 1);
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(acc_full(b), (uint32_t)(i >> 1) & 1, a.status));
+            if (!ok) break;
+            tc::tc_fence_after();
+            const int64_t t = blockIdx.x + i * gridDim.x;
+            const int64_t q = (t / a.splits) * kRows + r;
+            const int col0 = (int)(t % a.splits) * a.nc;
+            const bool valid = q < a.rows;
+            // next-mode layout of output (q, i): position jq + p' (rq + (R / n') i)
+            int64_t jq = 0, rq = 0;
+            if (!a.last) { jq = q % a.next_n; rq = q / a.next_n; }
+            const uint32_t set = tmem + lane_off + (uint32_t)(b * 2 * a.nc);
+            for (int c = 0; c < a.nc / 16; ++c) {
+                uint32_t vm[16], vc[16];
+                tc::tmem_ld16(set + (uint32_t)(c * 16), vm);
+                tc::tmem_ld16(set + (uint32_t)(a.nc + c * 16), vc);
+                tc::tmem_wait_ld();
+                if (!valid) continue;
+                const int i0 = col0 + c * 16;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int col = i0 + u;
+                    if (col >= a.n) break;
+                    const float y = __uint_as_float(vc[u]) + __uint_as_float(vm[u]);
+                    if (a.last) {
+                        a.yout[q + a.rows * (int64_t)col] = y;
+                    } else {
+                        const int64_t pos = jq + (int64_t)a.next_p * (rq + a.next_rows_per_i * col);
+                        store_parts<F>(a.pout, a.out_part_pitch, pos, y, 0.f);
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(acc_empty(b));
         }
     }
 
-    // ---- epilogue: all eight warps drain TMEM, partial sums added in FP32 ----
-    __syncwarp();
-    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(accum, 0, a.status));
-    tc::tc_fence_after();
-    if (ok) {
-        const int quarter = warp & 3, half = warp >> 2;
-        const int r = quarter * 32 + lane;
-        const int64_t q = q0 + r;
-        const bool valid = q < a.rows;
-        const int64_t base = valid ? (q % a.L) + (q / a.L) * a.L * a.n : 0;
-        const int chunks = a.nc / 16;
-        const int c_lo = half ? (chunks + 1) / 2 : 0;
-        const int c_hi = half ? chunks : (chunks + 1) / 2;
-        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        float alphaf = 0.f, t0f = 0.f, t1f = 0.f;
-        if constexpr (LAST) { alphaf = (float)e.alpha; t0f = (float)e.t0; t1f = (float)e.t1; }
-        for (int c = c_lo; c < c_hi; ++c) {
-            // y = corrections + main groups, added in FP32 (round to nearest)
-            float y[16];
-            uint32_t v[16];
-            tc::tmem_ld16(tmem + lane_off + (uint32_t)(a.groups * a.nc + c * 16), v);
-            tc::tmem_wait_ld();
-#pragma unroll
-            for (int t = 0; t < 16; ++t) y[t] = __uint_as_float(v[t]);
-            for (int g = 0; g < a.groups; ++g) {
-                tc::tmem_ld16(tmem + lane_off + (uint32_t)(g * a.nc + c * 16), v);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int t = 0; t < 16; ++t) y[t] += __uint_as_float(v[t]);
-            }
-            if (!valid) continue;
-            const int i0 = col0 + c * 16;
-            if constexpr (LAST) {
-                mixed_epilogue16(e, y, base, i0, a.n, a.L, alphaf, t0f, t1f);
-            } else if (a.L == 1 && (a.n & 3) == 0 && i0 + 16 <= a.n) {
-                float4* o = (float4*)(a.out + base + i0);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) o[t] = make_float4(y[4 * t], y[4 * t + 1], y[4 * t + 2], y[4 * t + 3]);
-            } else {
-#pragma unroll
-                for (int t = 0; t < 16; ++t)
-                    if (i0 + t < a.n) a.out[base + (int64_t)(i0 + t) * a.L] = y[t];
-            }
-        }
-    }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, a.tmem_cols);
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // Phi image of one K-block: rows i < n_img of kBK values j for each of the three
@@ -436,17 +281,17 @@ __global__ void build_phi_image_kernel(const double* __restrict__ phi, int n, in
         const double v = (i < n && j < n) ? phi[i + (int64_t)n * j] : 0.0;
         uint8_t* blk = img + (size_t)kb * kBParts * n_img * 128;
         const uint32_t off = sw_off<F>(i, c);
-        double r = v;
+        double rr = v;
         for (int part = 0; part < kBParts; ++part) {
             uint8_t* dst = blk + (size_t)part * n_img * 128 + off;
             if (F::kElem == 4) {
-                const float b = mx::tf32((float)r);
-                *(float*)dst = b;
-                r -= (double)b;
+                const float bq = mx::tf32((float)rr);
+                *(float*)dst = bq;
+                rr -= (double)bq;
             } else {
-                const __nv_bfloat16 b = __float2bfloat16_rn((float)r);
-                *(__nv_bfloat16*)dst = b;
-                r -= (double)__bfloat162float(b);
+                const __nv_bfloat16 bq = __float2bfloat16_rn((float)rr);
+                *(__nv_bfloat16*)dst = bq;
+                rr -= (double)__bfloat162float(bq);
             }
         }
     }
@@ -455,31 +300,22 @@ __global__ void build_phi_image_kernel(const double* __restrict__ phi, int n, in
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Geometry {
-    int n, n_img, nkb, nc, splits, groups, stages;
-    uint32_t tmem_cols;
+    int n, n_img, nkb, nc, splits, stages;
     size_t smem;
 };
 
-// Columns per CTA (nc, one MMA), accumulator groups, pipeline depth.
+// Columns per CTA (nc <= 128, one MMA), pipeline depth.
 template <class F>
 int geometry(int n, Geometry* g) {
     const int n16 = round_up(n, 16);
     if (n16 > 512) return MM_ERR_UNSUPPORTED;
     g->n = n;
     g->nkb = (n + F::kBK - 1) / F::kBK;
-    // columns per CTA: at most kNcMax, so that two pipeline stages of the A parts
-    // and the three Phi parts fit in shared memory
-    g->splits = (n16 + F::kNcMax - 1) / F::kNcMax;
+    g->splits = (n16 + kNcMax - 1) / kNcMax;
     g->nc = round_up((n16 + g->splits - 1) / g->splits, 16);
     g->n_img = g->splits * g->nc;
-    g->groups = std::min(std::min(g->nkb, kMaxGroups), std::max(1, 512 / g->nc - 1));
-    const int cols = (g->groups + 1) * g->nc;
-    uint32_t pow2 = 32;
-    while (pow2 < (uint32_t)cols) pow2 <<= 1;
-    if (pow2 > 512) return MM_ERR_UNSUPPORTED;
-    g->tmem_cols = pow2;
     const size_t stage = (size_t)F::kAParts * kATile + kBParts * (size_t)g->nc * 128;
-    const size_t fixed = 1024 + (3 * kMaxStages + 1) * 8 + 16;
+    const size_t fixed = 1024 + kBars * 8 + 16;
     int st = (int)((kSmemLimit - fixed) / stage);
     st = std::min(st, kMaxStages);
     if (st < 2) return MM_ERR_UNSUPPORTED;
@@ -492,34 +328,59 @@ int geometry_for(int prec, int n, Geometry* g) {
     return prec == MM_BF16X3 ? geometry<FormBF16>(n, g) : geometry<FormTF32>(n, g);
 }
 
-template <class F, typename TIn, bool LAST>
-int launch_mode(const Tf32Mode& m, const Epi& e, size_t smem, int64_t ctas, cudaStream_t s) {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+template <class F>
+int launch_form(const TcMode& m, const PartView& in, size_t smem, int64_t ctas, cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        MM_CUDA_TRY(cudaFuncSetAttribute(tc_mode_kernel<F, TIn, LAST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit));
+        MM_CUDA_TRY(cudaFuncSetAttribute(tc_mode_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemLimit));
         configured = true;
     }
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return MM_ERR_CUDA;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)in.n, (cuuint64_t)in.rows, (cuuint64_t)F::kAParts};
+    const cuuint64_t strides[2] = {(cuuint64_t)in.p * F::kElem, (cuuint64_t)in.part_pitch * F::kElem};
+    const cuuint32_t box[3] = {(cuuint32_t)F::kBK, (cuuint32_t)kRows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = F::kElem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (enc(&map, dt, 3, (void*)in.base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return MM_ERR_CUDA;
     TraceScope tr(KC_CONTRACT_TF32, s);
-    tc_mode_kernel<F, TIn, LAST><<<(unsigned)ctas, 256, smem, s>>>(m, e);
+    tc_mode_kernel<F><<<(unsigned)ctas, kThreads, smem, s>>>(m, map);
     MM_LAUNCH_CHECK();
     return MM_OK;
 }
 
-template <class F>
-int launch_form(const Tf32Mode& m, const Epi& e, bool in_fp64, bool last, size_t smem, int64_t ctas,
-                cudaStream_t s) {
-    if (in_fp64) {
-        return last ? launch_mode<F, double, true>(m, e, smem, ctas, s)
-                    : launch_mode<F, double, false>(m, e, smem, ctas, s);
-    }
-    return last ? launch_mode<F, float, true>(m, e, smem, ctas, s)
-                : launch_mode<F, float, false>(m, e, smem, ctas, s);
-}
-
 }  // namespace
 
+int form_elem_bytes(int prec) { return prec == MM_BF16X3 ? FormBF16::kElem : FormTF32::kElem; }
+int form_parts(int prec) { return prec == MM_BF16X3 ? FormBF16::kAParts : FormTF32::kAParts; }
+int form_pitch(int prec, int n) { return round_up(n, 16 / form_elem_bytes(prec)); }
+
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s) {
+    if (!encode_fn()) return MM_ERR_UNSUPPORTED;
     for (int mu = 0; mu < p->d; ++mu) {
         Geometry g;
         int rc = geometry_for(p->prec, (int)p->n[mu], &g);
@@ -549,29 +410,53 @@ int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s) {
     return MM_OK;
 }
 
-int tf32_mode_product(mm_plan_s* p, int ell, int mu, const void* in, bool in_fp64, float* out,
-                      const Epi* last, cudaStream_t s) {
+PartView mode_input_view(const mm_plan_s* p, int mu, uint8_t* base) {
+    PartView v;
+    v.base = base;
+    v.n = (int)p->n[mu - 1];
+    v.p = form_pitch(p->prec, v.n);
+    v.rows = p->N / v.n;
+    v.part_pitch = v.rows * v.p;
+    return v;
+}
+
+size_t part_set_bytes(const mm_plan_s* p) {
+    size_t mxb = 0;
+    for (int mu = 1; mu <= p->d; ++mu) {
+        const PartView v = mode_input_view(p, mu, nullptr);
+        const size_t b = (size_t)form_parts(p->prec) * (size_t)v.part_pitch * form_elem_bytes(p->prec);
+        mxb = std::max(mxb, (b + 255) / 256 * 256);
+    }
+    return mxb;
+}
+
+int tc_mode_product(mm_plan_s* p, int ell, int mu, const PartView& in, uint8_t* out_parts, float* yout,
+                    cudaStream_t s) {
     Geometry g;
     int rc = geometry_for(p->prec, (int)p->n[mu - 1], &g);
     if (rc) return rc;
-    Tf32Mode m{};
-    m.n = g.n; m.n_pad = g.n_img; m.nkb = g.nkb; m.nc = g.nc; m.splits = g.splits;
-    m.groups = g.groups; m.stages = g.stages;
-    int64_t L = 1;
-    for (int v = 0; v < mu - 1; ++v) L *= p->n[v];
-    m.L = L;
+    TcMode m{};
+    m.n = g.n; m.nkb = g.nkb; m.nc = g.nc; m.splits = g.splits; m.stages = g.stages; m.n_img = g.n_img;
     m.rows = p->N / g.n;
-    m.in = in;
-    m.out = out;
+    m.row_tiles = (m.rows + kRows - 1) / kRows;
     m.bimg = (const uint8_t*)p->phi_split[mu - 1][ell];
-    m.tmem_cols = g.tmem_cols;
     m.status = p->status;
-    const int64_t ctas = (m.rows + kRows - 1) / kRows * g.splits;
-    if (ctas > 0x7fffffffLL) return MM_ERR_SHAPE;
-    Epi e{};
-    if (last) e = *last;
-    if (p->prec == MM_BF16X3) return launch_form<FormBF16>(m, e, in_fp64, last != nullptr, g.smem, ctas, s);
-    return launch_form<FormTF32>(m, e, in_fp64, last != nullptr, g.smem, ctas, s);
+    m.last = mu == p->d;
+    if (m.last) {
+        m.yout = yout;
+    } else {
+        const PartView nx = mode_input_view(p, mu + 1, out_parts);
+        m.pout = out_parts;
+        m.out_part_pitch = nx.part_pitch;
+        m.next_n = nx.n;
+        m.next_p = nx.p;
+        m.next_rows_per_i = m.rows / nx.n;
+    }
+    if (m.rows > 0x7fffffffLL) return MM_ERR_SHAPE;
+    const int64_t tiles = m.row_tiles * g.splits;
+    const int64_t ctas = std::min<int64_t>(tiles, num_sms());
+    if (p->prec == MM_BF16X3) return launch_form<FormBF16>(m, in, g.smem, ctas, s);
+    return launch_form<FormTF32>(m, in, g.smem, ctas, s);
 }
 
 int tf32_supported(int prec, int n) {
