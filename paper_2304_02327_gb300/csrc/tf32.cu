@@ -17,19 +17,28 @@
 //           a0 b0 | a1 b0 + a0 b1 + a0 b2
 //   BF16x3: x = a0 + a1 + a2 (BF16, residual ~2^-25), Phi in 3 parts, 6 MMAs
 //           a0 b0 | a1 b0 + a0 b1 + a2 b0 + a1 b1 + a0 b2
-// The main product goes to one TMEM accumulator and the corrections to a
-// companion one, added in FP32 by the epilogue, so the small terms never round a
-// full-magnitude sum.  The three-way split of the fixed matrix keeps its rounding,
-// which would repeat identically every step, at 2^-33.
+// The tensor cores' FP32 accumulation truncates toward zero, which biases long
+// sums (measured: a one-sided relative error growing with K).  So the main
+// product of each K-block goes into a fresh TMEM slot (only its four MMAs
+// accumulate in hardware) and the epilogue warps add the slots into FP32 registers
+// with round-to-nearest; the much smaller corrections accumulate in TMEM over the
+// whole tile.  The three-way split of the fixed matrix keeps its rounding, which
+// would repeat identically every step, at 2^-33.
 //
 // Kernel structure: persistent, one CTA per SM over tiles t = blockIdx.x + i grid.
 //   warp 0      loader: per K-block, one TMA tensor load per operand part (the
 //               3-D map {K, rows, part} zero-fills the ragged K tail and the last
 //               rows) and bulk copies of this tile's columns of the plan's Phi image
-//   warp 1      MMA issuer (one thread), accumulator sets alternate between tiles
-//   warps 2-5   epilogue: drain TMEM (two sets: the epilogue of tile i overlaps the
-//               MMAs of tile i + 1), split the FP32 result into the next mode's
-//               parts (or write FP32 after the last mode)
+//   warp 1      MMA issuer (one thread): per K-block the main product into slot
+//               (K-block mod 2) of a two-slot ring, corrections into the tile's
+//               accumulator (two, alternating between tiles)
+//   warps 2-17  epilogue, four warps per TMEM lane quarter, each owning a quarter
+//               of the columns: drain each main slot into register accumulators as
+//               it completes (all chunk loads issued before one wait), then add the
+//               corrections and write the next mode's split operand (or FP32 after
+//               the last mode); the two-slot ring lets the MMAs of the next tile's
+//               first K-blocks run meanwhile
+// TMEM: [main slot 0 | main slot 1 | corr tile-even | corr tile-odd], nc each.
 // Every mbarrier wait is bounded (tcgen05.cuh).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -54,9 +63,12 @@ constexpr uint32_t kATile = kRows * 128;   // bytes of one operand part tile (12
 constexpr int kMaxStages = 4;
 constexpr int kBParts = 3;                 // Phi = b0 + b1 + b2 in both forms
 constexpr int kNcMax = 128;                // two sets of [main | corr] fit 512 TMEM columns
-constexpr int kBars = 2 * kMaxStages + 5;  // full, empty per stage; acc_full/empty x2; mma_done
+constexpr int kBars = 2 * kMaxStages + 9;  // full, empty per stage; main full/empty (slot);
+                                           // corr full/empty (tile parity); mma_done
 constexpr int kSmemLimit = 227 * 1024;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kQuartCols = kNcMax / 4;     // columns per epilogue thread (upper bound)
 
 template <class F> __device__ __forceinline__ uint32_t idesc_of(int nc);
 template <> __device__ __forceinline__ uint32_t idesc_of<FormTF32>(int nc) { return tc::idesc_tf32(128, nc); }
@@ -114,9 +126,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
     uint32_t* tmem_slot = (uint32_t*)(bars + kBars);
     auto full = [&](int s) { return tc::smem_u32(bars + s); };
     auto empty = [&](int s) { return tc::smem_u32(bars + kMaxStages + s); };
-    auto acc_full = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + b); };
-    auto acc_empty = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 2 + b); };
-    const uint32_t mma_done = tc::smem_u32(bars + 2 * kMaxStages + 4);
+    // Parity waits are only sound for a waiter that consumes every phase in order:
+    // the "full" barriers are waited only by the epilogue (in K-block / tile
+    // order), the "empty" ones only by the MMA thread.
+    auto mfull = [&](int r) { return tc::smem_u32(bars + 2 * kMaxStages + r); };
+    auto mempty = [&](int r) { return tc::smem_u32(bars + 2 * kMaxStages + 2 + r); };
+    auto cfull = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 4 + b); };
+    auto cempty = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 6 + b); };
+    const uint32_t mma_done = tc::smem_u32(bars + 2 * kMaxStages + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int stages = a.stages;
@@ -129,8 +146,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             tc::mbar_init(empty(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
-            tc::mbar_init(acc_full(b), 1);
-            tc::mbar_init(acc_empty(b), 4);
+            tc::mbar_init(mfull(b), 1);
+            tc::mbar_init(mempty(b), kEpiWarps);
+            tc::mbar_init(cfull(b), 1);
+            tc::mbar_init(cempty(b), kEpiWarps);
         }
         tc::mbar_init(mma_done, 1);
         tc::fence_mbar_init();
@@ -183,46 +202,82 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             // ---- MMA issuer ----
             const uint32_t id = idesc_of<F>(a.nc);
             int64_t it = 0;
+            int64_t uses[2] = {0, 0};      // uses of each main slot so far
             bool ok = true;
             for (int64_t i = 0; i < my_tiles && ok; ++i) {
                 const int b = (int)(i & 1);
-                if (i >= 2 && !tc::mbar_wait(acc_empty(b), (uint32_t)((i >> 1) - 1) & 1, a.status)) break;
-                tc::tc_fence_after();
-                const uint32_t mainacc = tmem + (uint32_t)(b * 2 * a.nc);
-                const uint32_t corr = mainacc + (uint32_t)a.nc;
+                if (i >= 2 && !tc::mbar_wait(cempty(b), (uint32_t)((i >> 1) - 1) & 1, a.status)) break;
+                const uint32_t corr = tmem + (uint32_t)((2 + b) * a.nc);
                 for (int kb = 0; kb < a.nkb; ++kb, ++it) {
                     const int s = (int)(it % stages);
+                    const int r = (int)(it & 1);
+                    if (uses[r] >= 1 && !tc::mbar_wait(mempty(r), (uint32_t)(uses[r] - 1) & 1, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    ++uses[r];
                     if (!tc::mbar_wait(full(s), (uint32_t)(it / stages) & 1, a.status)) { ok = false; break; }
                     tc::tc_fence_after();
+                    const uint32_t mainacc = tmem + (uint32_t)(r * a.nc);
                     const uint32_t abase = tc::smem_u32(smem + s * stage_bytes);
                     const uint32_t bbase = abase + a_bytes;
-#pragma unroll
+#pragma unroll 1
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint32_t ko = kk * 32;
-                        const uint32_t acc = (kb | kk) != 0;
-                        mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), id, acc);
+                        mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), id, kk != 0);
 #pragma unroll
                         for (int c = 0; c < F::kCorr; ++c)
                             mma<F>(corr, tc::desc_k_sw128(abase + F::corr_a(c) * kATile + ko),
                                    tc::desc_k_sw128(bbase + F::corr_b(c) * b_tile + ko), id,
-                                   c == 0 ? acc : 1u);
+                                   (c == 0 && (kb | kk) == 0) ? 0u : 1u);
                     }
                     tc::mma_commit(empty(s));
+                    tc::mma_commit(mfull(r));
                 }
-                if (ok) tc::mma_commit(acc_full(b));
+                if (ok) tc::mma_commit(cfull(b));
             }
             // every issued MMA has completed before TMEM can be released
             tc::mma_commit(mma_done);
             tc::mbar_wait(mma_done, 0, a.status);
         }
     } else {
-        // ---- epilogue: lane quarter (warp mod 4), one row per thread ----
+        // ---- epilogue: lane quarter (warp mod 4), column quarter ((warp - 2) / 4) ----
         const int quarter = warp & 3;
+        const int cq = (warp - 2) >> 2;
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const int nch = a.nc / 16;                        // <= 8 chunks of 16 columns
+        const int c0 = 2 * cq, c1 = min(nch, 2 * cq + 2);
         for (int64_t i = 0; i < my_tiles; ++i) {
             const int b = (int)(i & 1);
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(acc_full(b), (uint32_t)(i >> 1) & 1, a.status));
+            float acc[kQuartCols];
+#pragma unroll
+            for (int u = 0; u < kQuartCols; ++u) acc[u] = 0.f;
+            bool ok = true;
+            // main product, one K-block slot at a time, summed in FP32 registers
+            for (int kb = 0; kb < a.nkb && ok; ++kb) {
+                const int64_t it = i * a.nkb + kb;
+                const int rs = (int)(it & 1);
+                ok = __all_sync(0xffffffffu, tc::mbar_wait(mfull(rs), (uint32_t)(it >> 1) & 1, a.status));
+                if (!ok) break;
+                tc::tc_fence_after();
+                const uint32_t slot = tmem + lane_off + (uint32_t)(rs * a.nc);
+#pragma unroll
+                for (int c = 0; c < kQuartCols / 16; ++c) {
+                    if (c0 + c < c1) {          // warp-uniform
+                        uint32_t v[16];
+                        tc::tmem_ld16(slot + (uint32_t)((c0 + c) * 16), v);
+                        tc::tmem_wait_ld();
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) acc[c * 16 + u] += __uint_as_float(v[u]);
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(mempty(rs));
+            }
+            if (!ok) break;
+            ok = __all_sync(0xffffffffu, tc::mbar_wait(cfull(b), (uint32_t)(i >> 1) & 1, a.status));
             if (!ok) break;
             tc::tc_fence_after();
             const int64_t t = blockIdx.x + i * gridDim.x;
@@ -232,30 +287,40 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             // next-mode layout of output (q, i): position jq + p' (rq + (R / n') i)
             int64_t jq = 0, rq = 0;
             if (!a.last) { jq = q % a.next_n; rq = q / a.next_n; }
-            const uint32_t set = tmem + lane_off + (uint32_t)(b * 2 * a.nc);
-            for (int c = 0; c < a.nc / 16; ++c) {
-                uint32_t vm[16], vc[16];
-                tc::tmem_ld16(set + (uint32_t)(c * 16), vm);
-                tc::tmem_ld16(set + (uint32_t)(a.nc + c * 16), vc);
-                tc::tmem_wait_ld();
-                if (!valid) continue;
-                const int i0 = col0 + c * 16;
+            const uint32_t cset = tmem + lane_off + (uint32_t)((2 + b) * a.nc);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int col = i0 + u;
-                    if (col >= a.n) break;
-                    const float y = __uint_as_float(vc[u]) + __uint_as_float(vm[u]);
-                    if (a.last) {
-                        a.yout[q + a.rows * (int64_t)col] = y;
-                    } else {
-                        const int64_t pos = jq + (int64_t)a.next_p * (rq + a.next_rows_per_i * col);
-                        store_parts<F>(a.pout, a.out_part_pitch, pos, y, 0.f);
-                    }
+            for (int c = 0; c < kQuartCols / 16; ++c) {    // y = corrections + main, in FP32
+                if (c0 + c < c1) {
+                    uint32_t w[16];
+                    tc::tmem_ld16(cset + (uint32_t)((c0 + c) * 16), w);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) acc[c * 16 + u] += __uint_as_float(w[u]);
                 }
             }
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(acc_empty(b));
+            if (lane == 0) tc::mbar_arrive(cempty(b));      // corrections read: TMEM set free
+            if (!valid) continue;
+            // output column col of row q: next-mode position jq + p' (rq + (R / n') col)
+            // (or q + R col after the last mode); successive columns step by dpos
+            const int64_t dpos = a.last ? a.rows : (int64_t)a.next_p * a.next_rows_per_i;
+#pragma unroll
+            for (int c = 0; c < kQuartCols / 16; ++c) {
+                if (c0 + c >= c1) continue;
+                const int i0 = col0 + (c0 + c) * 16;
+                int64_t pos = a.last ? q + a.rows * (int64_t)i0
+                                     : jq + (int64_t)a.next_p * (rq + a.next_rows_per_i * (int64_t)i0);
+                const int lim = min(16, a.n - i0);
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    if (u >= lim) break;
+                    const float y = acc[c * 16 + u];
+                    if (a.last) a.yout[pos] = y;
+                    else store_parts<F>(a.pout, a.out_part_pitch, pos, y, 0.f);
+                    pos += dpos;
+                }
+            }
         }
     }
 
