@@ -42,3 +42,14 @@ def phisplit_apply(V: np.ndarray, phis, ell: int) -> np.ndarray:
     d = V.ndim
     scale = float(math.factorial(ell)) ** (d - 1)
     return tucker(scale * np.asarray(V, dtype=np.float64), phis)
+
+
+def phisplit_apply_at(V: np.ndarray, phis, ell: int, index_sets) -> np.ndarray:
+    """The entries of P_l^(2) on the grid index_sets[0] x ... x index_sets[d-1]
+    (index_sets[mu-1] lists values of i_mu), for checks on tensors too large to
+    transform in full.  Restricting the output index i_mu of a mu-mode product to a
+    set I is the mu-mode product with the rows I of the matrix, so this is the
+    same Tucker chain (Section 3) with phis[mu-1][I_mu, :].  Result shape:
+    (|I_d|, ..., |I_1|)."""
+    rows = [np.asarray(phi)[np.asarray(I, dtype=np.int64), :] for phi, I in zip(phis, index_sets)]
+    return phisplit_apply(V, rows, ell)

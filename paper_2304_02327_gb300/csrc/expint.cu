@@ -15,6 +15,19 @@
 
 namespace mm {
 
+PointwiseG pointwise_of(const mm_nonlin* g) {
+    PointwiseG pg{};
+    pg.kind = MM_G_NONE;
+    if (!g) return pg;
+    if (g->kind == MM_G_CUBIC || g->kind == MM_G_ADR_MANUFACTURED) {
+        pg.kind = g->kind;
+        pg.c0 = g->c[0]; pg.c1 = g->c[1]; pg.c2 = g->c[2]; pg.c3 = g->c[3];
+        pg.f0 = (float)g->c[0]; pg.f1 = (float)g->c[1]; pg.f2 = (float)g->c[2]; pg.f3 = (float)g->c[3];
+        pg.psi_a = g->psi_a; pg.psi_b = g->psi_b;
+    }
+    return pg;
+}
+
 namespace {
 
 double factorial(int k) {
@@ -58,19 +71,6 @@ double* free_during_last(const mm_plan_s* p, double* in, double* scratch) {
     if (p->d == 1) return scratch;
     // FP64: the last mode reads outs[d-2] = (d-2 even ? scratch : in)
     return (p->d % 2 == 0) ? in : scratch;
-}
-
-PointwiseG pointwise_of(const mm_nonlin* g) {
-    PointwiseG pg{};
-    pg.kind = MM_G_NONE;
-    if (!g) return pg;
-    if (g->kind == MM_G_CUBIC || g->kind == MM_G_ADR_MANUFACTURED) {
-        pg.kind = g->kind;
-        pg.c0 = g->c[0]; pg.c1 = g->c[1]; pg.c2 = g->c[2]; pg.c3 = g->c[3];
-        pg.f0 = (float)g->c[0]; pg.f1 = (float)g->c[1]; pg.f2 = (float)g->c[2]; pg.f3 = (float)g->c[3];
-        pg.psi_a = g->psi_a; pg.psi_b = g->psi_b;
-    }
-    return pg;
 }
 
 StencilArgs stencil_base(const mm_plan_s* p, const double* U, double* W, int mode, double t,
@@ -198,7 +198,7 @@ extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, 
 
 extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g) {
     if (!p) return 0;
-    if (p->prec != MM_FP64) return mixed_workspace_bytes(p, scheme);
+    if (p->prec != MM_FP64) return mixed_workspace_bytes(p, scheme, g ? g->kind : MM_G_NONE);
     const size_t N = (size_t)p->N;
     size_t buffers = 2;                          // Tucker ping-pong X, Y
     if (scheme == MM_ETD2RK) buffers = 3;        // + U2
@@ -233,8 +233,7 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
 
     cudaStream_t s = (cudaStream_t)stream;
     if (p->prec != MM_FP64) {
-        if (gk == MM_G_RICCATI) return MM_ERR_UNSUPPORTED;
-        return mixed_expint(p, scheme, pointwise_of(g), U, t0, nsteps, (uint8_t*)ws, s);
+        return mixed_expint(p, scheme, g, U, t0, nsteps, (uint8_t*)ws, s);
     }
     const int64_t N = p->N;
     double* X = (double*)ws;

@@ -10,8 +10,23 @@
 // ETD2RK, writes the split stage-2 input g(U2) - g(U) (formed in FP32 from its
 // difference expansion).
 //
-// Workspace, with S = part_set_bytes (one operand buffer) and N the state size:
+// Dense A_mu and the Riccati G (d = 2, U n1 x n2 column-major, Section 1 eq. (2)):
+// K u is split into the tridiagonal band of each A_mu, evaluated by the stencil
+// prepass from differences of the state, plus the remainders R_mu = A_mu - band:
+//   R1 U = X M^T with X = R1, M = U^T;    U R2^T with X = U, M = R2,
+// and U B U as (U B) U: first T = B^T U^T (X = B^T, M = U), written as parts of
+// U B with the contraction index fastest, then T U (X = U B, M = U^T).  The state
+// is split twice per evaluation (as M = U and as M = U^T); B once per call.  The
+// products land in FP32 (yk: the remainders, yq: U B U) and the prepass adds them
+// and C to the band stencil.  The tridiagonal band stays out of the tensor-core
+// products because its entries (~h^-2) would make their rounding dominate the
+// K u + G difference.
+//
+// Workspace, with S = part_set_bytes (one operand buffer) and N the state size,
+// every piece 256-byte aligned:
 //   [IN: S][P1: S][P2: S][IN2: S (Lawson2b)][y: 4N][pairs: 8N][U2: 8N]
+//   dense / Riccati: [Ut: U 3 parts][Un: U^T 3 parts][T: U B parts][Bx: B^T parts]
+//                    [yk: 4N][yq: 4N]
 #include <math.h>
 
 #include <algorithm>
@@ -57,6 +72,9 @@ __global__ void __launch_bounds__(256) mixed_update_kernel(const float* __restri
             store_parts_prec(e.prec, e.W2p, e.w2_pitch, pos, w2, 0.f);
             break;
         }
+        case EPI_ETD_S1_NOG:
+            e.U2[i] = fma(e.alpha, mx::f2d(yi), e.U[i]);
+            break;
         case EPI_ETD_S2: {
             const double v = fma(e.alpha, mx::f2d(yi), e.U2[i]);
             flag_nonfinite_bits(e, v);
@@ -87,7 +105,94 @@ __global__ void __launch_bounds__(256) split_input_kernel(const double* __restri
     }
 }
 
+// W2 = ya - yb as parts in the mode-1 layout (the Riccati stage-2 input).
+__global__ void __launch_bounds__(256) diff_split_kernel(const float* __restrict__ ya, const float* __restrict__ yb,
+                                                         uint8_t* parts, int64_t pitch, int n1, int p1, int prec,
+                                                         int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        store_parts_prec(prec, parts, pitch, (i % n1) + (int64_t)p1 * (i / n1), __ldg(ya + i) - __ldg(yb + i), 0.f);
+}
+
 int64_t grid_of(int64_t N) { return std::min<int64_t>((N + 255) / 256, (int64_t)num_sms() * 16); }
+
+struct Carve {
+    uint8_t* p;
+    size_t used = 0;
+    uint8_t* take(size_t bytes) {
+        uint8_t* q = p ? p + used : nullptr;
+        used += (bytes + 255) / 256 * 256;
+        return q;
+    }
+};
+
+// The workspace pieces of expint_mixed (see the layout above).
+struct MixedWs {
+    uint8_t *IN, *P1, *P2, *IN2;
+    float* y;
+    float2* pairs;
+    double* U2;
+    uint8_t *Ut, *Un, *T, *Bx;
+    float *yk, *yq;
+    size_t bytes;
+};
+
+MixedWs carve_ws(const mm_plan_s* p, bool dense, uint8_t* base) {
+    // the base is 16-byte aligned; start the pieces on a 256-byte boundary
+    uint8_t* b0 = base ? (uint8_t*)(((uintptr_t)base + 255) & ~(uintptr_t)255) : nullptr;
+    Carve c{b0};
+    MixedWs w{};
+    const size_t S = part_set_bytes(p);
+    const size_t N = (size_t)p->N;
+    w.IN = c.take(S); w.P1 = c.take(S); w.P2 = c.take(S); w.IN2 = c.take(S);
+    w.y = (float*)c.take(4 * N);
+    w.pairs = (float2*)c.take(8 * N);
+    w.U2 = (double*)c.take(8 * N);
+    if (dense) {
+        const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+        w.Ut = c.take(matrix_parts_bytes(p->prec, n1, n2, 3));
+        w.Un = c.take(matrix_parts_bytes(p->prec, n2, n1, 3));
+        w.T = c.take(matrix_parts_bytes(p->prec, n1, n1, 3));
+        w.Bx = c.take(matrix_parts_bytes(p->prec, n1, n2, 3));
+        w.yk = (float*)c.take(4 * N);
+        w.yq = (float*)c.take(4 * N);
+    }
+    w.bytes = c.used + 256;
+    return w;
+}
+
+// For the state U: yk = R1 U + U R2^T (rem) and yq = U B U (ubu).
+int dense_products(mm_plan_s* p, const double* U, bool rem, bool ubu, float* yk, float* yq, const MixedWs& w,
+                   cudaStream_t s) {
+    const int prec = p->prec;
+    const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+    const PartView Ut = matrix_view(prec, w.Ut, n1, n2);     // M = U   (rows i1, k = i2)
+    const PartView Un = matrix_view(prec, w.Un, n2, n1);     // M = U^T (rows i2, k = i1)
+    int rc = split_matrix(prec, U, n1, 1, 0, Ut, 3, s);
+    if (!rc) rc = split_matrix(prec, U, n1, 0, 0, Un, 3, s);
+    if (rc) return rc;
+    TcOut o{};
+    o.last = 1; o.ldy = n1;
+    if (rem) {
+        o.y = yk; o.accum = 0;
+        rc = tc_product(prec, Ut, matrix_view(prec, (uint8_t*)p->rem_split[1], n2, n2), o, p->status, s);
+        if (rc) return rc;
+        o.accum = 1;
+        rc = tc_product(prec, matrix_view(prec, (uint8_t*)p->rem_split[0], n1, n1), Un, o, p->status, s);
+        if (rc) return rc;
+    }
+    if (ubu) {
+        const PartView T = matrix_view(prec, w.T, n1, n1);    // U B, rows i1
+        TcOut ot{};
+        ot.last = 0; ot.parts = w.T; ot.part_pitch = T.part_pitch;
+        ot.next_n = n1; ot.next_p = T.p; ot.next_rows_per_i = 1;
+        rc = tc_product(prec, matrix_view(prec, w.Bx, n1, n2), Ut, ot, p->status, s);
+        if (rc) return rc;
+        o.y = yq; o.accum = 0;
+        rc = tc_product(prec, T, Un, o, p->status, s);
+    }
+    return rc;
+}
 
 }  // namespace
 
@@ -121,30 +226,42 @@ size_t mixed_mumode_workspace_bytes(const mm_plan_s* p) {
     return 3 * part_set_bytes(p) + (size_t)p->N * sizeof(float) + 256;
 }
 
-size_t mixed_workspace_bytes(const mm_plan_s* p, int scheme) {
-    const size_t S = part_set_bytes(p);
-    const size_t N = (size_t)p->N;
-    return 4 * S + N * (4 + 8 + 8) + 1024;
+size_t mixed_workspace_bytes(const mm_plan_s* p, int scheme, int gkind) {
+    (void)scheme;
+    return carve_ws(p, !p->tridiag || gkind == MM_G_RICCATI, nullptr).bytes;
 }
 
-int mixed_expint(mm_plan_s* p, int scheme, const PointwiseG& pg, double* U, double t0, int nsteps,
+int mixed_expint(mm_plan_s* p, int scheme, const mm_nonlin* gd, double* U, double t0, int nsteps,
                  uint8_t* ws, cudaStream_t s) {
-    if (!p->tridiag) return MM_ERR_UNSUPPORTED;
+    const bool riccati = gd && gd->kind == MM_G_RICCATI;
+    const bool dense = !p->tridiag || riccati;
+    if (dense && (p->d != 2 || (!p->tridiag && !p->rem_split[0]))) return MM_ERR_UNSUPPORTED;
+    if (riccati && scheme != MM_EXPEULER && scheme != MM_ETD2RK) return MM_ERR_UNSUPPORTED;
+    const PointwiseG pg = pointwise_of(gd);
+    const MixedWs w = carve_ws(p, dense, ws);
+    uint8_t* IN = w.IN;
+    uint8_t* P1 = w.P1;
+    uint8_t* P2 = w.P2;
+    uint8_t* IN2 = w.IN2;
+    float* y = w.y;
+    float2* pairs = w.pairs;
+    double* U2 = w.U2;
     const int64_t N = p->N;
-    const size_t S = part_set_bytes(p);
-    uint8_t* IN = ws;
-    uint8_t* P1 = IN + S;
-    uint8_t* P2 = P1 + S;
-    uint8_t* IN2 = P2 + S;
-    float* y = (float*)(IN2 + S);
-    float2* pairs = (float2*)(((uintptr_t)(y + N) + 255) & ~(uintptr_t)255);
-    double* U2 = (double*)(pairs + N);
+    int rc = MM_OK;
+    if (riccati) {   // X = B^T: B is n2 x n1 column-major
+        rc = split_matrix(p->prec, gd->B, p->n[1], 0, 0, matrix_view(p->prec, w.Bx, p->n[0], (int)p->n[1]),
+                          form_parts(p->prec), s);
+        if (rc) return rc;
+    }
     const double tau = p->tau;
     const int d = p->d;
     const PartView in1 = mode_input_view(p, 1, IN);
 
     StencilArgsMixed a{};
     a.d = d; a.N = N; a.U = U; a.g = pg;
+    a.yadd = !p->tridiag ? w.yk : nullptr;
+    a.yadd2 = riccati ? w.yq : nullptr;
+    a.cadd = riccati ? gd->C : nullptr;
     a.part_pitch = in1.part_pitch; a.p1 = in1.p; a.prec = p->prec;
     int64_t st = 1;
     for (int mu = 0; mu < d; ++mu) {
@@ -154,10 +271,13 @@ int mixed_expint(mm_plan_s* p, int scheme, const PointwiseG& pg, double* U, doub
         a.coef[mu] = p->coef3f[mu];
     }
 
-    int rc = MM_OK;
     for (int k = 0; k < nsteps && rc == MM_OK; ++k) {
         const double t = t0 + k * tau;
         a.t = (float)t;
+        if (dense && (scheme == MM_EXPEULER || scheme == MM_ETD2RK)) {
+            rc = dense_products(p, U, !p->tridiag, riccati, w.yk, w.yq, w, s);
+            if (rc) break;
+        }
         switch (scheme) {
         case MM_EXPEULER: {
             a.mode = PRE_KU_G; a.Wp = IN; a.W2p = nullptr;
@@ -173,11 +293,20 @@ int mixed_expint(mm_plan_s* p, int scheme, const PointwiseG& pg, double* U, doub
             rc = launch_prepass_mixed(a, pairs, s);
             if (rc) break;
             Epi e1{};
-            e1.kind = EPI_ETD_S1; e1.alpha = tau; e1.U = U; e1.U2 = U2;
+            e1.kind = riccati ? EPI_ETD_S1_NOG : EPI_ETD_S1; e1.alpha = tau; e1.U = U; e1.U2 = U2;
             e1.W2p = IN; e1.w2_pitch = in1.part_pitch; e1.w2_n = in1.n; e1.w2_p = in1.p;
             e1.t0 = t; e1.t1 = t + tau; e1.g = pg; e1.status = p->status;
             rc = mixed_tucker(p, 1, IN, P1, P2, y, e1, s);
             if (rc) break;
+            if (riccati) {   // W2 = G(U2) - G(U) = U2 B U2 - U B U
+                // U2 B U2 into yk (the remainders in it are used up)
+                rc = dense_products(p, U2, false, true, nullptr, w.yk, w, s);
+                if (rc) break;
+                TraceScope tr(KC_SPLIT, s);
+                diff_split_kernel<<<(unsigned)grid_of(N), 256, 0, s>>>(w.yk, w.yq, IN, in1.part_pitch, in1.n,
+                                                                        in1.p, p->prec, N);
+                MM_LAUNCH_CHECK();
+            }
             Epi e2{};
             e2.kind = EPI_ETD_S2; e2.alpha = tau * pow(2.0, d - 1); e2.U = U; e2.U2 = U2;
             e2.status = p->status;

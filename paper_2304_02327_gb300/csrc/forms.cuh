@@ -58,6 +58,21 @@ __device__ __forceinline__ void store_parts(uint8_t* base, int64_t part_pitch, i
     }
 }
 
+// Three parts of (x + xl) in both forms (the operand that every product multiplies
+// with all of the other side's parts: a phi matrix, a remainder of A, the state as
+// the matrix side of a Riccati product).  The first kAParts parts equal those of
+// split_parts, so one three-part array also serves as a kAParts-part operand.
+template <class F> __device__ __forceinline__ void split_parts3(float x, float xl, uint32_t (&p)[3]);
+template <> __device__ __forceinline__ void split_parts3<FormTF32>(float x, float xl, uint32_t (&p)[3]) {
+    const float h = mx::tf32(x);
+    const float r = (x - h) + xl;
+    const float l = mx::tf32(r);
+    p[0] = __float_as_uint(h); p[1] = __float_as_uint(l); p[2] = __float_as_uint(mx::tf32(r - l));
+}
+template <> __device__ __forceinline__ void split_parts3<FormBF16>(float x, float xl, uint32_t (&p)[3]) {
+    split_parts<FormBF16>(x, xl, p);
+}
+
 // Runtime dispatch on the plan's precision for elementwise writers.
 __device__ __forceinline__ void store_parts_prec(int prec, uint8_t* base, int64_t part_pitch, int64_t pos,
                                                  float x, float xl) {

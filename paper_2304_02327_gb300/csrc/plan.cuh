@@ -25,10 +25,11 @@ struct mm_plan_s {
     double* A[MM_MAX_D] = {};          // device copy of A_mu (column-major)
     double* diag3[MM_MAX_D] = {};      // [sub | main | super] of A_mu
     double* phi[MM_MAX_D][4] = {};     // phi_l(tau A_mu), FP64, column-major
-    // TF32x3 form: per direction and l, the pre-split operand images the
-    // tensor-core kernel loads (layout in tf32.cu).
+    // Mixed forms: per direction and l, phi_l(tau A_mu) split into three parts
+    // (matrix operand layout of tf32.cuh).
     float* phi_split[MM_MAX_D][4] = {};
     float* coef3f[MM_MAX_D] = {};      // mixed K u stencil: [a | c | row sum] per direction
+    float* rem_split[MM_MAX_D] = {};   // mixed, dense A (d = 2): parts of A_mu minus its band
     unsigned int* status = nullptr;    // device status word (MM_STATUS_* bits)
     std::vector<void*> owned;
 

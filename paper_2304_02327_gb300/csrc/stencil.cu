@@ -102,6 +102,13 @@ __global__ void __launch_bounds__(256) prepass_mixed_kernel(StencilArgsMixed a) 
                     acc = fmaf(cf[nm + i], (v.x - uh) + (v.y - ul), acc);
                 }
             }
+            if (a.yadd) acc += __ldg(a.yadd + off);
+            if (a.yadd2) acc += __ldg(a.yadd2 + off);
+            if (a.cadd) {
+                float ch, cl;
+                mx::d2ff(__ldg(a.cadd + off), ch, cl);
+                acc += ch + cl;
+            }
             const int64_t pos = (off % a.n[0]) + (int64_t)a.p1 * (off / a.n[0]);
             store_parts_prec(a.prec, a.Wp, a.part_pitch, pos, acc, 0.f);
         } else {

@@ -25,7 +25,7 @@ int launch_prepass(const StencilArgs& a, cudaStream_t s);
 
 // Mixed-precision prepass (split-operand output from the FP64 state, no FP64
 // arithmetic; element idx goes to position (idx mod n_1) + p_1 (idx div n_1)):
-//   PRE_KU_G:   W = K u + g(t, u), K tridiagonal, written as
+//   PRE_KU_G:   W = K u + g(t, u) (+ yadd + yadd2 + cadd), K's tridiagonal band as
 //               sum_mu a (u_{i-1} - u_i) + c (u_{i+1} - u_i) + s u_i with the row
 //               sums s = a + b + c, the differences taken from the double-float
 //               split of the state (so they keep their own relative accuracy)
@@ -38,6 +38,9 @@ struct StencilArgsMixed {
     int64_t stride[MM_MAX_D];
     const float* coef[MM_MAX_D];    // [a | c | s] per direction, 3 n floats
     const double* U;
+    const float* yadd;              // PRE_KU_G: FP32 terms added to W, or NULL (dense
+    const float* yadd2;             //   parts of K u, U B U of a Riccati G)
+    const double* cadd;             // PRE_KU_G: FP64 term added to W (Riccati C), or NULL
     const float2* Up;               // U split once into (hi, lo) FP32 pairs (PRE_KU_G)
     uint8_t* Wp;                    // output parts (mode-1 layout)
     uint8_t* W2p;                   // second output parts (PRE_LAWSON), or NULL

@@ -91,16 +91,18 @@ __host__ __device__ __forceinline__ uint32_t sw_off(uint32_t row, uint32_t k) {
 }
 
 struct TcMode {
-    int n, nkb, nc, splits, stages, n_img;
-    int64_t rows, row_tiles;
-    const uint8_t* bimg;
-    // output: next mode's parts (layout above) or FP32 after the last mode
-    int last;
-    float* yout;
-    uint8_t* pout;           // part q at pout + q * out_part_pitch elements
+    int k;                   // contraction length (row length of both operands)
+    int ncols;               // output columns = rows of the matrix operand
+    int nkb, nc, splits, stages;
+    int64_t rows, row_tiles; // rows of the tensor operand (output rows)
+    // output: split parts in the layout below, or FP32 (stored or added)
+    int last, accum;
+    float* yout;             // y[q + ldy col]
+    int64_t ldy;
+    uint8_t* pout;           // part j at pout + j * out_part_pitch elements
     int64_t out_part_pitch;  // elements per part
-    int next_n, next_p;      // next mode's fibre length and row pitch
-    int64_t next_rows_per_i; // R_mu / n_{mu+1}
+    int next_n, next_p;      // fibre length and row pitch of the output layout
+    int64_t next_rows_per_i; // rows of the output layout per output column
     unsigned int* status;
 };
 
@@ -116,7 +118,8 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
 
 
 template <class F>
-__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __grid_constant__ CUtensorMap amap) {
+__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __grid_constant__ CUtensorMap amap,
+                                                            const __grid_constant__ CUtensorMap bmap) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t b_tile = (uint32_t)a.nc * 128u;
@@ -165,10 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- loader: operand parts by TMA, Phi columns by bulk copy ----
+            // ---- loader: both operands' parts by TMA ----
             int64_t issued_last[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) issued_last[s] = -1;
-            const size_t kb_bytes = (size_t)kBParts * a.n_img * 128;   // one K-block of the image
             const int64_t total = my_tiles * a.nkb;
             for (int64_t it = 0; it < total; ++it) {
                 const int s = (int)(it % stages);
@@ -181,15 +183,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
                 const uint32_t st = tc::smem_u32(smem + s * stage_bytes);
                 for (int q = 0; q < F::kAParts; ++q)
                     tma_load_3d(st + q * kATile, &amap, kb * F::kBK, row0, q, full(s));
-                for (int part = 0; part < kBParts; ++part) {  // b0 rows, b1 rows, b2 rows
-                    const uint8_t* src = a.bimg + (size_t)kb * kb_bytes +
-                                         (size_t)part * a.n_img * 128 + (size_t)col0 * 128;
-                    const uint32_t d0 = st + a_bytes + part * b_tile;
-                    for (uint32_t off = 0; off < b_tile; off += 16384) {
-                        const uint32_t len = min(16384u, b_tile - off);
-                        tc::bulk_g2s(d0 + off, src + off, len, full(s));
-                    }
-                }
+                for (int part = 0; part < kBParts; ++part)   // rows col0.. of b0, b1, b2
+                    tma_load_3d(st + a_bytes + part * b_tile, &bmap, kb * F::kBK, col0, part, full(s));
                 issued_last[s] = it;
             }
             // never leave the CTA with copies in flight
@@ -304,19 +299,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             if (!valid) continue;
             // output column col of row q: next-mode position jq + p' (rq + (R / n') col)
             // (or q + R col after the last mode); successive columns step by dpos
-            const int64_t dpos = a.last ? a.rows : (int64_t)a.next_p * a.next_rows_per_i;
+            const int64_t dpos = a.last ? a.ldy : (int64_t)a.next_p * a.next_rows_per_i;
 #pragma unroll
             for (int c = 0; c < kQuartCols / 16; ++c) {
                 if (c0 + c >= c1) continue;
                 const int i0 = col0 + (c0 + c) * 16;
-                int64_t pos = a.last ? q + a.rows * (int64_t)i0
+                int64_t pos = a.last ? q + a.ldy * (int64_t)i0
                                      : jq + (int64_t)a.next_p * (rq + a.next_rows_per_i * (int64_t)i0);
-                const int lim = min(16, a.n - i0);
+                const int lim = min(16, a.ncols - i0);
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     if (u >= lim) break;
                     const float y = acc[c * 16 + u];
-                    if (a.last) a.yout[pos] = y;
+                    if (a.last) a.yout[pos] = a.accum ? a.yout[pos] + y : y;
                     else store_parts<F>(a.pout, a.out_part_pitch, pos, y, 0.f);
                     pos += dpos;
                 }
@@ -330,34 +325,45 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// Phi image of one K-block: rows i < n_img of kBK values j for each of the three
-// parts b0, b1, b2 in turn (Phi = b0 + b1 + b2, each rounded to the form's type
-// in turn), K-major, 128-byte swizzled, zero outside the n x n matrix.
-template <class F>
-__global__ void build_phi_image_kernel(const double* __restrict__ phi, int n, int n_img, int nkb,
-                                       uint8_t* __restrict__ img) {
-    const int64_t total = (int64_t)nkb * n_img * F::kBK;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(t % F::kBK);
-        const int i = (int)((t / F::kBK) % n_img);
-        const int kb = (int)(t / ((int64_t)F::kBK * n_img));
-        const int j = kb * F::kBK + c;
-        const double v = (i < n && j < n) ? phi[i + (int64_t)n * j] : 0.0;
-        uint8_t* blk = img + (size_t)kb * kBParts * n_img * 128;
-        const uint32_t off = sw_off<F>(i, c);
-        double rr = v;
-        for (int part = 0; part < kBParts; ++part) {
-            uint8_t* dst = blk + (size_t)part * n_img * 128 + off;
-            if (F::kElem == 4) {
-                const float bq = mx::tf32((float)rr);
-                *(float*)dst = bq;
-                rr -= (double)bq;
-            } else {
-                const __nv_bfloat16 bq = __float2bfloat16_rn((float)rr);
-                *(__nv_bfloat16*)dst = bq;
-                rr -= (double)__bfloat162float(bq);
-            }
+// Matrix operand M (rows x K, M[i][k]) -> its parts at dst[j part_pitch + k + pitch i],
+// from the FP64 matrix `src`: src[i + ld k] if colmajor (M itself stored column-major)
+// else src[k + ld i] (M^T stored column-major).  zero_band drops |i - k| <= 1 (the
+// tridiagonal band, evaluated apart as a stencil).  32 x 32 tiles through shared
+// memory, so both the read and the write are coalesced.
+template <class F, int NP>
+__global__ void __launch_bounds__(256) split_matrix_kernel(const double* __restrict__ src, int64_t ld, int rows,
+                                                           int K, int colmajor, int zero_band, uint8_t* dst,
+                                                           int pitch, int64_t part_pitch) {
+    __shared__ double t[32][33];          // t[k - k0][i - i0]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int k0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int y = ty + 8 * r;
+        if (colmajor) {                    // lanes along i
+            const int i = i0 + tx, k = k0 + y;
+            t[y][tx] = (i < rows && k < K) ? __ldg(src + i + ld * k) : 0.0;
+        } else {                           // lanes along k
+            const int i = i0 + y, k = k0 + tx;
+            t[tx][y] = (i < rows && k < K) ? __ldg(src + k + ld * i) : 0.0;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty + 8 * r, k = k0 + tx;
+        if (i >= rows || k >= K) continue;
+        double v = t[tx][ty + 8 * r];
+        if (zero_band && i - k <= 1 && k - i <= 1) v = 0.0;
+        float h, l;
+        mx::d2ff(v, h, l);
+        uint32_t pp[3];
+        split_parts3<F>(h, l, pp);
+        const int64_t pos = k + (int64_t)pitch * i;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            if (F::kElem == 4) ((uint32_t*)dst)[j * part_pitch + pos] = pp[j];
+            else ((uint16_t*)dst)[j * part_pitch + pos] = (uint16_t)pp[j];
         }
     }
 }
@@ -365,20 +371,34 @@ __global__ void build_phi_image_kernel(const double* __restrict__ phi, int n, in
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Geometry {
-    int n, n_img, nkb, nc, splits, stages;
+    int nkb, nc, splits, stages;
     size_t smem;
 };
 
-// Columns per CTA (nc <= 128, one MMA), pipeline depth.
+// Output columns per CTA tile (nc <= 128, one MMA) and pipeline depth.  Among the
+// column splittings with nc a multiple of 16, take the one whose tile waves over
+// the SMs cost least, a tile costing its columns plus a fixed 32-column-equivalent
+// overhead (the operand tile re-read, the epilogue's fixed work).
 template <class F>
-int geometry(int n, Geometry* g) {
-    const int n16 = round_up(n, 16);
-    if (n16 > 512) return MM_ERR_UNSUPPORTED;
-    g->n = n;
-    g->nkb = (n + F::kBK - 1) / F::kBK;
-    g->splits = (n16 + kNcMax - 1) / kNcMax;
-    g->nc = round_up((n16 + g->splits - 1) / g->splits, 16);
-    g->n_img = g->splits * g->nc;
+int geometry(int K, int ncols, int64_t rows, Geometry* g) {
+    if (K < 1 || ncols < 1 || rows < 1) return MM_ERR_SHAPE;
+    const int n16 = round_up(ncols, 16);
+    const int64_t row_tiles = (rows + kRows - 1) / kRows;
+    const int64_t sms = num_sms();
+    const int s_min = (n16 + kNcMax - 1) / kNcMax;
+    int64_t best = -1;
+    for (int sp = s_min; sp <= 2 * s_min && sp <= n16 / 16; ++sp) {
+        const int nc = round_up((n16 + sp - 1) / sp, 16);
+        const int splits = (n16 + nc - 1) / nc;
+        const int64_t waves = (row_tiles * splits + sms - 1) / sms;
+        const int64_t cost = waves * (nc + 32);
+        if (best < 0 || cost < best) {
+            best = cost;
+            g->nc = nc;
+            g->splits = splits;
+        }
+    }
+    g->nkb = (K + F::kBK - 1) / F::kBK;
     const size_t stage = (size_t)F::kAParts * kATile + kBParts * (size_t)g->nc * 128;
     const size_t fixed = 1024 + kBars * 8 + 16;
     int st = (int)((kSmemLimit - fixed) / stage);
@@ -387,10 +407,6 @@ int geometry(int n, Geometry* g) {
     g->stages = st;
     g->smem = fixed + st * stage;
     return MM_OK;
-}
-
-int geometry_for(int prec, int n, Geometry* g) {
-    return prec == MM_BF16X3 ? geometry<FormBF16>(n, g) : geometry<FormTF32>(n, g);
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
@@ -412,28 +428,56 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
+// 3-D map {K, rows, parts} of a part array, box {one K-block, box_rows, 1 part},
+// 128-byte swizzle; loads past K or the last row read zeros.
 template <class F>
-int launch_form(const TcMode& m, const PartView& in, size_t smem, int64_t ctas, cudaStream_t s) {
+int encode_parts(CUtensorMap* map, const PartView& v, int nparts, int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return MM_ERR_UNSUPPORTED;
+    if (((uintptr_t)v.base & 15) || ((int64_t)v.p * F::kElem) % 16 || (v.part_pitch * F::kElem) % 16)
+        return MM_ERR_ARG;
+    const cuuint64_t dims[3] = {(cuuint64_t)v.n, (cuuint64_t)v.rows, (cuuint64_t)nparts};
+    const cuuint64_t strides[2] = {(cuuint64_t)v.p * F::kElem, (cuuint64_t)v.part_pitch * F::kElem};
+    const cuuint32_t box[3] = {(cuuint32_t)F::kBK, (cuuint32_t)box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = F::kElem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (enc(map, dt, 3, (void*)v.base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return MM_ERR_CUDA;
+    return MM_OK;
+}
+
+template <class F>
+int launch_form(const PartView& X, const PartView& M, const TcOut& o, unsigned int* status, cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
         MM_CUDA_TRY(cudaFuncSetAttribute(tc_mode_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemLimit));
         configured = true;
     }
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return MM_ERR_CUDA;
-    CUtensorMap map;
-    const cuuint64_t dims[3] = {(cuuint64_t)in.n, (cuuint64_t)in.rows, (cuuint64_t)F::kAParts};
-    const cuuint64_t strides[2] = {(cuuint64_t)in.p * F::kElem, (cuuint64_t)in.part_pitch * F::kElem};
-    const cuuint32_t box[3] = {(cuuint32_t)F::kBK, (cuuint32_t)kRows, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = F::kElem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    if (enc(&map, dt, 3, (void*)in.base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return MM_ERR_CUDA;
+    if (X.n != M.n || X.rows > 0x7fffffffLL || M.rows > 0x7fffffffLL) return MM_ERR_SHAPE;
+    Geometry g;
+    int rc = geometry<F>(X.n, (int)M.rows, X.rows, &g);
+    if (rc) return rc;
+    TcMode m{};
+    m.k = X.n; m.ncols = (int)M.rows;
+    m.nkb = g.nkb; m.nc = g.nc; m.splits = g.splits; m.stages = g.stages;
+    m.rows = X.rows;
+    m.row_tiles = (X.rows + kRows - 1) / kRows;
+    m.last = o.last; m.accum = o.accum;
+    m.yout = o.y; m.ldy = o.ldy;
+    m.pout = o.parts; m.out_part_pitch = o.part_pitch;
+    m.next_n = o.next_n; m.next_p = o.next_p; m.next_rows_per_i = o.next_rows_per_i;
+    m.status = status;
+    if (!m.last && (m.next_n < 1 || m.next_p < m.next_n)) return MM_ERR_ARG;
+    CUtensorMap amap, bmap;
+    if ((rc = encode_parts<F>(&amap, X, F::kAParts, kRows))) return rc;
+    if ((rc = encode_parts<F>(&bmap, M, kBParts, g.nc))) return rc;
+    const int64_t tiles = m.row_tiles * g.splits;
+    const int64_t ctas = std::min<int64_t>(tiles, num_sms());
     TraceScope tr(KC_CONTRACT_TF32, s);
-    tc_mode_kernel<F><<<(unsigned)ctas, kThreads, smem, s>>>(m, map);
+    tc_mode_kernel<F><<<(unsigned)ctas, kThreads, g.smem, s>>>(m, amap, bmap);
     MM_LAUNCH_CHECK();
     return MM_OK;
 }
@@ -444,32 +488,74 @@ int form_elem_bytes(int prec) { return prec == MM_BF16X3 ? FormBF16::kElem : For
 int form_parts(int prec) { return prec == MM_BF16X3 ? FormBF16::kAParts : FormTF32::kAParts; }
 int form_pitch(int prec, int n) { return round_up(n, 16 / form_elem_bytes(prec)); }
 
+PartView matrix_view(int prec, uint8_t* base, int64_t rows, int K) {
+    PartView v;
+    v.base = base;
+    v.n = K;
+    v.p = form_pitch(prec, K);
+    v.rows = rows;
+    v.part_pitch = rows * v.p;
+    return v;
+}
+
+size_t matrix_parts_bytes(int prec, int64_t rows, int K, int nparts) {
+    const size_t b = (size_t)nparts * rows * form_pitch(prec, K) * form_elem_bytes(prec);
+    return (b + 255) / 256 * 256;
+}
+
+int split_matrix(int prec, const double* src, int64_t ld, int colmajor, int zero_band, const PartView& dst,
+                 int nparts, cudaStream_t s) {
+    if (nparts < 2 || nparts > 3 || dst.rows > 0x7fffffffLL) return MM_ERR_ARG;
+    const dim3 grid((unsigned)((dst.n + 31) / 32), (unsigned)((dst.rows + 31) / 32));
+    if (grid.y > 65535) return MM_ERR_SHAPE;
+    TraceScope tr(KC_SPLIT, s);
+    const int rows = (int)dst.rows;
+#define MM_SPLIT_LAUNCH(F, NP)                                                                            \
+    split_matrix_kernel<F, NP><<<grid, 256, 0, s>>>(src, ld, rows, dst.n, colmajor, zero_band, dst.base, \
+                                                     dst.p, dst.part_pitch)
+    if (prec == MM_BF16X3) {
+        if (nparts == 3) MM_SPLIT_LAUNCH(FormBF16, 3);
+        else MM_SPLIT_LAUNCH(FormBF16, 2);
+    } else {
+        if (nparts == 3) MM_SPLIT_LAUNCH(FormTF32, 3);
+        else MM_SPLIT_LAUNCH(FormTF32, 2);
+    }
+#undef MM_SPLIT_LAUNCH
+    MM_LAUNCH_CHECK();
+    return MM_OK;
+}
+
+int tc_product(int prec, const PartView& X, const PartView& M, const TcOut& o, unsigned int* status,
+               cudaStream_t s) {
+    if (prec == MM_BF16X3) return launch_form<FormBF16>(X, M, o, status, s);
+    return launch_form<FormTF32>(X, M, o, status, s);
+}
+
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s) {
     if (!encode_fn()) return MM_ERR_UNSUPPORTED;
     for (int mu = 0; mu < p->d; ++mu) {
-        Geometry g;
-        int rc = geometry_for(p->prec, (int)p->n[mu], &g);
-        if (rc) return rc;
         if (p->owner[mu] != mu) {
             for (int l = 0; l <= p->ell_max; ++l) p->phi_split[mu][l] = p->phi_split[p->owner[mu]][l];
             p->coef3f[mu] = p->coef3f[p->owner[mu]];
+            p->rem_split[mu] = p->rem_split[p->owner[mu]];
             continue;
         }
+        const int n = (int)p->n[mu];
         if (!p->alloc((void**)&p->coef3f[mu], 3 * p->n[mu] * sizeof(float))) return MM_ERR_NOMEM;
-        rc = build_stencil_coef(p->A[mu], (int)p->n[mu], p->coef3f[mu], s);
+        int rc = build_stencil_coef(p->A[mu], n, p->coef3f[mu], s);
         if (rc) return rc;
-        const size_t bytes = (size_t)g.nkb * kBParts * g.n_img * 128;
-        const int bk = p->prec == MM_BF16X3 ? FormBF16::kBK : FormTF32::kBK;
+        const size_t bytes = matrix_parts_bytes(p->prec, n, n, kBParts);
         for (int l = 0; l <= p->ell_max; ++l) {
             if (!p->alloc((void**)&p->phi_split[mu][l], bytes)) return MM_ERR_NOMEM;
-            const int64_t total = (int64_t)g.nkb * g.n_img * bk;
-            const int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
-            uint8_t* img = (uint8_t*)p->phi_split[mu][l];
-            if (p->prec == MM_BF16X3)
-                build_phi_image_kernel<FormBF16><<<grid, 256, 0, s>>>(p->phi[mu][l], g.n, g.n_img, g.nkb, img);
-            else
-                build_phi_image_kernel<FormTF32><<<grid, 256, 0, s>>>(p->phi[mu][l], g.n, g.n_img, g.nkb, img);
-            MM_LAUNCH_CHECK();
+            rc = split_matrix(p->prec, p->phi[mu][l], n, 1, 0,
+                              matrix_view(p->prec, (uint8_t*)p->phi_split[mu][l], n, n), kBParts, s);
+            if (rc) return rc;
+        }
+        if (!p->tridiag && p->d == 2) {   // A_mu minus its band: the dense part of K u (d = 2)
+            if (!p->alloc((void**)&p->rem_split[mu], bytes)) return MM_ERR_NOMEM;
+            rc = split_matrix(p->prec, p->A[mu], n, 1, 1,
+                              matrix_view(p->prec, (uint8_t*)p->rem_split[mu], n, n), kBParts, s);
+            if (rc) return rc;
         }
     }
     return MM_OK;
@@ -497,36 +583,22 @@ size_t part_set_bytes(const mm_plan_s* p) {
 
 int tc_mode_product(mm_plan_s* p, int ell, int mu, const PartView& in, uint8_t* out_parts, float* yout,
                     cudaStream_t s) {
-    Geometry g;
-    int rc = geometry_for(p->prec, (int)p->n[mu - 1], &g);
-    if (rc) return rc;
-    TcMode m{};
-    m.n = g.n; m.nkb = g.nkb; m.nc = g.nc; m.splits = g.splits; m.stages = g.stages; m.n_img = g.n_img;
-    m.rows = p->N / g.n;
-    m.row_tiles = (m.rows + kRows - 1) / kRows;
-    m.bimg = (const uint8_t*)p->phi_split[mu - 1][ell];
-    m.status = p->status;
-    m.last = mu == p->d;
-    if (m.last) {
-        m.yout = yout;
+    const int n = (int)p->n[mu - 1];
+    const PartView M = matrix_view(p->prec, (uint8_t*)p->phi_split[mu - 1][ell], n, n);
+    TcOut o{};
+    o.last = mu == p->d;
+    if (o.last) {
+        o.y = yout;
+        o.ldy = in.rows;
     } else {
         const PartView nx = mode_input_view(p, mu + 1, out_parts);
-        m.pout = out_parts;
-        m.out_part_pitch = nx.part_pitch;
-        m.next_n = nx.n;
-        m.next_p = nx.p;
-        m.next_rows_per_i = m.rows / nx.n;
+        o.parts = out_parts;
+        o.part_pitch = nx.part_pitch;
+        o.next_n = nx.n;
+        o.next_p = nx.p;
+        o.next_rows_per_i = in.rows / nx.n;
     }
-    if (m.rows > 0x7fffffffLL) return MM_ERR_SHAPE;
-    const int64_t tiles = m.row_tiles * g.splits;
-    const int64_t ctas = std::min<int64_t>(tiles, num_sms());
-    if (p->prec == MM_BF16X3) return launch_form<FormBF16>(m, in, g.smem, ctas, s);
-    return launch_form<FormTF32>(m, in, g.smem, ctas, s);
-}
-
-int tf32_supported(int prec, int n) {
-    Geometry g;
-    return geometry_for(prec, n, &g);
+    return tc_product(p->prec, in, M, o, p->status, s);
 }
 
 }  // namespace mm

@@ -13,7 +13,7 @@ import pytest
 import scipy.linalg
 
 from oracle.phi import phi_matrices
-from oracle.tucker import mode_product, tucker, phisplit_apply
+from oracle.tucker import mode_product, tucker, phisplit_apply, phisplit_apply_at
 from paper_2304_02327_gb300 import workloads as wl
 
 
@@ -158,3 +158,22 @@ def test_split_at_tau_zero_is_phi_of_zero(ell):
     V = np.random.default_rng(9).standard_normal((3, 4, 5))
     P = phisplit_apply(V, [phi_matrices(np.zeros((n, n)), ell)[ell] for n in (5, 4, 3)], ell)
     assert np.abs(P - V / math.factorial(ell)).max() < 1e-15
+
+
+def test_phisplit_at_sampled_entries_element_loop():
+    """phisplit_apply_at on a sampled index grid equals the element loop of eq. (7)
+    with the (l!)^(d-1) factor, entry by entry (brute force, d = 3, l = 2)."""
+    rng = np.random.default_rng(31)
+    ns = (5, 4, 6)
+    phis = [rng.standard_normal((n, n)) for n in ns]
+    V = rng.standard_normal(tuple(reversed(ns)))
+    sets = [[4, 0, 2], [3], [1, 5]]
+    got = phisplit_apply_at(V, phis, 2, sets)
+    assert got.shape == (2, 1, 3)
+    for a3, i3 in enumerate(sets[2]):
+        for a2, i2 in enumerate(sets[1]):
+            for a1, i1 in enumerate(sets[0]):
+                acc = 0.0
+                for j3, j2, j1 in itertools.product(range(ns[2]), range(ns[1]), range(ns[0])):
+                    acc += phis[0][i1, j1] * phis[1][i2, j2] * phis[2][i3, j3] * V[j3, j2, j1]
+                assert abs(4.0 * acc - got[a3, a2, a1]) <= 1e-12 * max(1.0, abs(acc))
