@@ -167,6 +167,18 @@ def reference_arm(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
+    if args.workload in wl.BATCHED:
+        probs = wl.batched_workload(args.workload)
+        cb = oracle_batch_sample(probs, args.cpu_seconds)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": METRIC,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": args.workload, "precision": "fp64"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": METRIC, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
     p = wl.workload(args.workload)
     from oracle.integrators import OracleProblem, step
     op = OracleProblem.from_problem(p)
@@ -195,11 +207,210 @@ def reference_arm(args):
     return 0
 
 
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def tensor_peak(prec):
+    """(peak TFLOP/s, note) of the form's tensor-core dtype, from the measured BF16 peak."""
+    bf16 = float(measured_peaks().get("bf16_tflops", 1900.0))
+    if prec == "tf32x3":
+        return bf16 * TF32_NOMINAL_RATIO, (f"TF32 dense peak = measured bf16 {bf16:.1f} TFLOP/s "
+                                           "(MEASURED_PEAKS.json) x nominal TF32/BF16 ratio 1.1/2.25")
+    return bf16, f"BF16 dense peak measured {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json)"
+
+
+def ours_batched(args):
+    """Config 4: many independent 2D Allen-Cahn problems in one batch (mixed form)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2304_02327_gb300 import api
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    api.lib()
+    prec = args.prec if args.prec != "fp64" else "bf16x3"
+    probs_all = wl.batched_workload(args.workload)
+    costs = [parallel.instance_cost(p.n[0]) for p in probs_all]
+    mine = parallel.shard_for_rank(costs, rank, world)       # LPT shard, no collective
+    probs = [probs_all[i] for i in mine]
+    dof = sum(p.u0.size for p in probs)
+    dof_all = sum(p.u0.size for p in probs_all)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plans, gs, Us = api.setup_batch(probs, prec)
+    b = api.Batch(plans, gs, Us, autotune=True, graph=True)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.run(1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, one graph launch each, L2 flushed between ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    api.trace_enable(False)
+    for k in range(args.steps):
+        flush.fill_(k & 0xff)
+        starts[k].record(stream)
+        b.run(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = {c: api.trace_read(c, timed=False)[0] for c in (api.KC_CONTRACT_TF32, api.KC_PREPASS,
+                                                                api.KC_SPLIT)}
+    assert b.status() == 0, "non-finite state during the timed steps"
+    t_ms = parallel.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device="cuda")
+    value = parallel.job_throughput([dof_all * args.steps], t_ms / 1e3)
+
+    # ---- per-kernel device times: the same launches, eager and traced ----
+    bp = api.Batch(plans, gs, Us, autotune=False, nc_cap=b.info()["nc_cap"], graph=False)
+    bp.run(1)
+    torch.cuda.synchronize()
+    api.trace_enable(True)
+    ksteps = min(args.steps, 5)
+    for k in range(ksteps):
+        flush.fill_(k & 0xff)
+        bp.run(1)
+    torch.cuda.synchronize()
+    n_launch, k_ms = api.trace_read(api.KC_CONTRACT_TF32)
+    _, pre_ms = api.trace_read(api.KC_PREPASS)
+    _, upd_ms = api.trace_read(api.KC_SPLIT)
+    api.trace_enable(False)
+    bp.close()
+
+    # ---- e2e: every state in from pinned host memory, one step, every state out ----
+    hosts = [torch.from_numpy(np.ascontiguousarray(p.u0)).pin_memory() for p in probs]
+    e2e_steps = min(args.steps, 5)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(e2e_steps):
+        for h, u in zip(hosts, Us):
+            u.copy_(h, non_blocking=True)
+        b.run(1)
+        for h, u in zip(hosts, Us):
+            h.copy_(u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = parallel.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    e2e_value = parallel.job_throughput([dof_all * e2e_steps], e2e_ms / 1e3)
+
+    # ---- the per-instance FP64 GPU loop on the same shard, for comparison ----
+    fp_plans, fp_gs, fp_Us = api.setup_batch(probs, "fp64")
+    fp_ws = [api.expint_workspace(pl, wl.EXPEULER, g) for pl, g in zip(fp_plans, fp_gs)]
+    for pl, g, u, w in zip(fp_plans, fp_gs, fp_Us, fp_ws):
+        api.expint_step(pl, wl.EXPEULER, u, 1, g=g, ws=w)
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fsteps = 2
+    f0.record(stream)
+    for k in range(fsteps):
+        for pl, g, u, w in zip(fp_plans, fp_gs, fp_Us, fp_ws):
+            api.expint_step(pl, wl.EXPEULER, u, 1, g=g, ws=w)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp_ms = parallel.max_over_ranks(f0.elapsed_time(f1), device="cuda") / fsteps
+    del fp_plans, fp_gs, fp_Us, fp_ws
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    nprod = 4 if prec == "tf32x3" else 6
+    # logical flops of one grouped launch (one direction of every instance): 2 N_j n_mu
+    flops_launch = sum(2.0 * p.u0.size * p.n[0] for p in probs)
+    k_avg = k_ms / n_launch if n_launch else None
+    peak, note = tensor_peak(prec)
+    achieved = nprod * flops_launch / (k_avg / 1e3) / 1e12 if k_avg else None
+    info = b.info()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{prec}+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances": len(probs_all), "dof": dof_all,
+                   "sizes": "n uniform over {48, 64, ..., 512}, square", "scheme": "expeuler",
+                   "tau": probs_all[0].tau, "precision": prec, "size_classes": info["classes"],
+                   "nc_cap_autotuned": info["nc_cap"], "tiles_per_mode": info["tiles_mode1"],
+                   "graph": "one CUDA graph launch per step (4 kernels)",
+                   "l2": "flushed between timed steps (512 MB write); states 0.8 GB > L2",
+                   "parallelism": f"LPT shard of instances x{world}"},
+        "plan_ms": plan_ms,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": None,
+                     "kernel": "tc_mode_kernel (grouped tcgen05 mu-mode contraction, all instances)",
+                     "launches": n_launch, "avg_launch_ms": k_avg,
+                     "share_of_step_time": (k_ms / ksteps) / (t_ms / args.steps) if k_ms else None,
+                     "flops_per_launch": nprod * flops_launch,
+                     "timing": "eager traced run of the same launches (a graph replay has no "
+                               "per-kernel events)",
+                     "peak_note": note},
+        "elementwise_ms_per_step": {"prepass": pre_ms / ksteps, "update": upd_ms / ksteps},
+        "fp64_per_instance_loop": {"ms_per_step": fp_ms, "value": dof_all / (fp_ms / 1e3),
+                                   "unit": METRIC, "speedup_of_batch": fp_ms / (t_ms / args.steps)},
+        "e2e": {"value": e2e_value, "unit": METRIC, "steps": e2e_steps,
+                "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": dof * 8},
+        "gpu_launches": sum(launches.values()),
+        "launches_by_kernel": {"contract_tf32": launches[api.KC_CONTRACT_TF32],
+                               "prepass": launches[api.KC_PREPASS], "update": launches[api.KC_SPLIT]},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_batch_sample(probs_all, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def oracle_batch_sample(probs, seconds):
+    """The FP64 oracle on a bounded sample of the batch: whole instances (in the
+    batch's order, one step each) until the time is spent."""
+    from oracle.integrators import OracleProblem, step
+    t0 = time.perf_counter()
+    dof = 0
+    k = 0
+    while k < len(probs) and time.perf_counter() - t0 < seconds:
+        p = probs[k]
+        op = OracleProblem.from_problem(p, lmax=1)
+        step(op, np.array(p.u0, dtype=np.float64), p.scheme, 0.0)
+        dof += p.u0.size
+        k += 1
+    dt = time.perf_counter() - t0
+    return {"value": dof / dt, "unit": METRIC, "cores": host_cores(), "kind": "oracle",
+            "sample": f"one step of each of the first {k} instances (phi set-up included, "
+                      f"numpy float64, {dt:.1f} s)"}
+
+
 def ours(args):
     import torch
     import torch.distributed as dist
     from paper_2304_02327_gb300 import api
 
+    if args.workload in wl.BATCHED:
+        return ours_batched(args)
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
     if world > 1:

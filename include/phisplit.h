@@ -232,6 +232,74 @@ MM_API int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, dou
 MM_API int tucker_apply_noalloc(int d, const int64_t* n, const double* const* M,
                                 const double* V, double* P, double alpha, void* stream);
 
+/* ---- batches of independent problems ------------------------------------
+ * Many independent 2D problems of uneven size (exponential Euler, eq. (19)),
+ * advanced together in a mixed form: instances of equal (n1, n2) share packed
+ * operand buffers, and each step is four launches for the whole batch (the
+ * K u + g prepass, one persistent tensor-core launch per direction over the tiles
+ * of every instance, the FP64 update), captured once in a CUDA graph.
+ *
+ * mm_tune: autotune = 1 times the candidate tile widths nc in {128, 96, 64} on the
+ * batch's own Tucker launches at creation and keeps the fastest; nc_cap = 16..128
+ * (a multiple of 16) fixes the width instead (0: autotune or 128); graph = 1 makes
+ * expint_batch_run replay a captured graph of its nsteps steps (0: plain launches).
+ * A NULL mm_tune means {autotune 0, nc_cap 0, graph 1}. */
+typedef struct mm_tune {
+    int autotune;
+    int nc_cap;
+    int graph;
+} mm_tune;
+
+typedef struct mm_batch_s* mm_batch;
+
+/*
+ * expint_batch_create -- prepare `count` instances for batched stepping.
+ *   plans  host array of count plans: all d = 2, the same mixed precision
+ *          (MM_TF32X3 or MM_BF16X3), tridiagonal A_mu, ell_max >= 1; each plan's
+ *          own tau is used for its instance.  The plans must outlive the batch.
+ *   g      host array of count descriptors (MM_G_NONE or MM_G_CUBIC), or NULL.
+ *   U      host array of count device pointers, n1 x n2 doubles each (i_1
+ *          fastest), 8-byte aligned; the batch updates them in place.
+ *   scheme MM_EXPEULER (others: MM_ERR_UNSUPPORTED).
+ * Allocates the batch's device memory (packed operands: about 2 (parts) x 2 +
+ * 4 bytes of FP32 result per element, plus each instance's phi_1 parts), copies
+ * the instances' phi_1 parts, builds the tile lists (and autotunes), then
+ * synchronises `stream`.  Errors: MM_ERR_ARG, MM_ERR_UNSUPPORTED, MM_ERR_SHAPE,
+ * MM_ERR_NOMEM, MM_ERR_CUDA; *out is NULL on error.
+ */
+MM_API int expint_batch_create(mm_batch* out, int count, const mm_plan* plans, const mm_nonlin* g,
+                               double* const* U, int scheme, const mm_tune* tune, void* stream);
+
+/* nsteps steps of every instance, stream-ordered, no synchronisation.  With the
+ * graph option the first run with a given nsteps captures the steps (on a stream
+ * of the batch) and every run replays the graph on `stream`.  t0 is the time of
+ * the first step (the supported g are autonomous).  Errors: MM_ERR_ARG,
+ * MM_ERR_CUDA. */
+MM_API int expint_batch_run(mm_batch b, double t0, int nsteps, void* stream);
+
+/* Synchronises `stream`; OR of MM_STATUS_* raised by the batch (>= 0). */
+MM_API int expint_batch_status(mm_batch b, int reset, void* stream);
+
+/* Host query: number of size classes, the tile width in use, mode-1 tiles per
+ * step, total degrees of freedom.  Any pointer may be NULL. */
+MM_API int expint_batch_info(mm_batch b, int* nclasses, int* nc_cap, int64_t* tiles_mode1,
+                             int64_t* total_dof);
+
+/* Frees the batch (synchronises the device).  NULL is OK. */
+MM_API int expint_batch_destroy(mm_batch b);
+
+/* One-shot: create, run nsteps, synchronise, destroy. */
+MM_API int expint_batched(int count, const mm_plan* plans, const mm_nonlin* g, double* const* U,
+                          int scheme, double t0, int nsteps, const mm_tune* tune, void* stream);
+
+/* Host-only (no device work): the tile list a batch of these sizes uses for one
+ * direction (mode 1 or 2) at tile width nc_cap, tiles of decreasing cost.  Each
+ * tile is 4 ints {instance, row tile, column split, size class}; pass tiles =
+ * NULL to get the count only.  Errors: MM_ERR_ARG, MM_ERR_SHAPE,
+ * MM_ERR_UNSUPPORTED (more than 32 size classes). */
+MM_API int mm_batch_tile_plan(int count, const int64_t* n1, const int64_t* n2, int prec, int nc_cap,
+                              int mode, int32_t* tiles, int64_t max_tiles, int64_t* ntiles);
+
 /* ---- launch tracing --------------------------------------------------
  * Kernel classes counted by the library.  Counting is always on; with tracing
  * enabled every launch is also bracketed by a pair of CUDA events recorded on

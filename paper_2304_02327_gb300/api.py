@@ -34,7 +34,9 @@ PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3, "bf16x3": MM_BF16X3}
 EXPORTS = ("phi_plan_create", "phi_plan_destroy", "phi_plan_info", "phi_plan_get_phi",
            "phi_plan_status", "mumode_workspace_bytes", "mumode_phi_apply",
            "expint_workspace_bytes", "expint_step", "mm_status_str", "mm_version",
-           "mm_trace_enable", "mm_trace_read", "tucker_apply_noalloc")
+           "mm_trace_enable", "mm_trace_read", "tucker_apply_noalloc",
+           "expint_batch_create", "expint_batch_run", "expint_batch_status", "expint_batch_info",
+           "expint_batch_destroy", "expint_batched", "mm_batch_tile_plan")
 KC_CONTRACT_FP64, KC_CONTRACT_TF32, KC_PREPASS, KC_SPLIT = 0, 1, 2, 3
 
 
@@ -49,6 +51,11 @@ class Nonlin(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("c", ctypes.c_double * 4),
                 ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
                 ("psi_a", ctypes.c_void_p), ("psi_b", ctypes.c_void_p)]
+
+
+class Tune(ctypes.Structure):
+    """mm_tune of include/phisplit.h."""
+    _fields_ = [("autotune", ctypes.c_int), ("nc_cap", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 _lib = None
@@ -81,6 +88,14 @@ def lib():
     L.mm_status_str.restype = ctypes.c_char_p
     L.mm_version.argtypes = []
     L.tucker_apply_noalloc.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(vp), vp, vp, f64, vp]
+    P = ctypes.POINTER
+    L.expint_batch_create.argtypes = [P(vp), i32, P(vp), P(Nonlin), P(vp), i32, P(Tune), vp]
+    L.expint_batch_run.argtypes = [vp, f64, i32, vp]
+    L.expint_batch_status.argtypes = [vp, i32, vp]
+    L.expint_batch_info.argtypes = [vp, P(i32), P(i32), P(i64), P(i64)]
+    L.expint_batch_destroy.argtypes = [vp]
+    L.expint_batched.argtypes = [i32, P(vp), P(Nonlin), P(vp), i32, f64, i32, P(Tune), vp]
+    L.mm_batch_tile_plan.argtypes = [i32, P(i64), P(i64), i32, i32, i32, P(ctypes.c_int32), i64, P(i64)]
     L.mm_trace_enable.argtypes = [i32]
     L.mm_trace_read.argtypes = [i32, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(f64)]
     for name in EXPORTS:
@@ -267,3 +282,82 @@ def setup(problem: "wl.Problem", prec: str = "fp64", ell_max: Optional[int] = No
     g = Nonlinearity.from_problem(problem)
     U = torch.from_numpy(np.ascontiguousarray(problem.u0)).cuda()
     return plan, g, U
+
+
+class Batch:
+    """expint_batch_create / run / destroy: many independent 2D problems stepped
+    together in a mixed form (one graph launch per run)."""
+
+    def __init__(self, plans: Sequence[Plan], gs: Optional[Sequence[Optional[Nonlinearity]]],
+                 Us: Sequence[torch.Tensor], scheme: int = EXPEULER, autotune: bool = True,
+                 nc_cap: int = 0, graph: bool = True, stream=None):
+        L = lib()
+        self.plans = list(plans)
+        self.Us = list(Us)
+        self.gs = list(gs) if gs is not None else None
+        n = len(self.plans)
+        h_arr = (ctypes.c_void_p * n)(*[p.handle.value for p in self.plans])
+        u_arr = (ctypes.c_void_p * n)(*[_ptr(u) for u in self.Us])
+        g_arr = None
+        if self.gs is not None:
+            g_arr = (Nonlin * n)()
+            for j, g in enumerate(self.gs):
+                if g is not None:
+                    g_arr[j] = g.struct
+        self.tune = Tune(int(autotune), int(nc_cap), int(graph))
+        h = ctypes.c_void_p()
+        _check(L.expint_batch_create(ctypes.byref(h), n, h_arr, g_arr, u_arr, int(scheme),
+                                     ctypes.byref(self.tune), _stream(stream)), "expint_batch_create")
+        self.handle = h
+
+    def run(self, nsteps: int, t0: float = 0.0, stream=None) -> None:
+        _check(lib().expint_batch_run(self.handle, float(t0), int(nsteps), _stream(stream)),
+               "expint_batch_run")
+
+    def status(self, reset: bool = True) -> int:
+        return _check(lib().expint_batch_status(self.handle, int(reset), _stream()), "expint_batch_status")
+
+    def info(self) -> dict:
+        nc, cap = ctypes.c_int(), ctypes.c_int()
+        t, dof = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().expint_batch_info(self.handle, ctypes.byref(nc), ctypes.byref(cap), ctypes.byref(t),
+                                       ctypes.byref(dof)), "expint_batch_info")
+        return {"classes": nc.value, "nc_cap": cap.value, "tiles_mode1": t.value, "dof": dof.value}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().expint_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_tile_plan(n1: Sequence[int], n2: Sequence[int], prec: str = "bf16x3", nc_cap: int = 128,
+                    mode: int = 1) -> np.ndarray:
+    """Host-only tile list of a batch (mm_batch_tile_plan): rows {instance, row tile,
+    column split, size class}, in launch order."""
+    L = lib()
+    cnt = len(n1)
+    a1 = (ctypes.c_int64 * cnt)(*[int(v) for v in n1])
+    a2 = (ctypes.c_int64 * cnt)(*[int(v) for v in n2])
+    nt = ctypes.c_int64()
+    _check(L.mm_batch_tile_plan(cnt, a1, a2, PRECISIONS[prec], int(nc_cap), int(mode), None, 0,
+                                ctypes.byref(nt)), "mm_batch_tile_plan")
+    buf = (ctypes.c_int32 * (4 * nt.value))()
+    _check(L.mm_batch_tile_plan(cnt, a1, a2, PRECISIONS[prec], int(nc_cap), int(mode), buf, nt.value,
+                                ctypes.byref(nt)), "mm_batch_tile_plan")
+    return np.frombuffer(buf, dtype=np.int32).reshape(-1, 4).copy()
+
+
+def setup_batch(problems: Sequence["wl.Problem"], prec: str = "bf16x3"):
+    """Plans, nonlinearities and device states of a list of independent problems."""
+    plans, gs, Us = [], [], []
+    for p in problems:
+        plans.append(Plan(p.A, p.tau, ell_for_scheme(p.scheme), prec))
+        gs.append(Nonlinearity.from_problem(p))
+        Us.append(torch.from_numpy(np.ascontiguousarray(p.u0)).cuda())
+    return plans, gs, Us

@@ -69,6 +69,7 @@ constexpr int kSmemLimit = 227 * 1024;
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kQuartCols = kNcMax / 4;     // columns per epilogue thread (upper bound)
+constexpr int kMaxClasses = MM_TC_MAX_CLASSES;
 
 template <class F> __device__ __forceinline__ uint32_t idesc_of(int nc);
 template <> __device__ __forceinline__ uint32_t idesc_of<FormTF32>(int nc) { return tc::idesc_tf32(128, nc); }
@@ -90,23 +91,34 @@ __host__ __device__ __forceinline__ uint32_t sw_off(uint32_t row, uint32_t k) {
            (k % per) * F::kElem;
 }
 
-struct TcMode {
-    int k;                   // contraction length (row length of both operands)
-    int ncols;               // output columns = rows of the matrix operand
-    int nkb, nc, splits, stages;
-    int64_t rows, row_tiles; // rows of the tensor operand (output rows)
-    // output: split parts in the layout below, or FP32 (stored or added)
-    int last, accum;
-    float* yout;             // y[q + ldy col]
-    int64_t ldy;
-    uint8_t* pout;           // part j at pout + j * out_part_pitch elements
-    int64_t out_part_pitch;  // elements per part
+// One class of tiles: instances of equal shape whose operands sit packed one after
+// the other (instance j's tensor operand rows at j * rows, its matrix operand rows
+// at j * ncols).  A single product is one class with one instance.
+struct TcClass {
+    CUtensorMap xmap;        // tensor operand parts {k, rows x instances, kAParts}
+    CUtensorMap mmap;        // matrix operand parts {k, ncols x instances, 3}
+    int k, ncols, nkb, nc, splits;
+    int rows;                // tensor operand rows (output rows) per instance
+    int last, accum;         // FP32 output (stored, or added when accum) / split parts
+    float* yout;             // instance j: y[j y_stride + q + ldy col]
+    int64_t ldy, y_stride;
+    uint8_t* pout;           // instance j: part m element j p_stride + layout position
+    int64_t out_part_pitch, p_stride;
     int next_n, next_p;      // fibre length and row pitch of the output layout
     int64_t next_rows_per_i; // rows of the output layout per output column
+};
+
+template <int C>
+struct TcGroup {
+    TcClass cls[C];
+    const int4* tiles;       // {class, instance, row tile, column split}; NULL: class 0,
+    int64_t ntiles;          //   instance 0, tile t = row tile (t / splits), split (t % splits)
+    int stage_nc;            // widest nc of the classes (shared-memory and TMEM slots)
+    int stages;
     unsigned int* status;
 };
 
-// 3-D TMA load of one part tile: box {K block, 128 rows} at (k0, row0, part).
+// 3-D TMA load of one part tile: box {K block, box rows} at (k0, row0, part).
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int k0, int row0, int part,
                                             uint32_t bar) {
     asm volatile(
@@ -116,16 +128,32 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+struct TileId {
+    int c, inst, rt, sp;
+};
 
-template <class F>
-__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __grid_constant__ CUtensorMap amap,
-                                                            const __grid_constant__ CUtensorMap bmap) {
+template <int C>
+__device__ __forceinline__ TileId tile_of(const TcGroup<C>& g, int64_t t) {
+    TileId id;
+    if (g.tiles) {
+        const int4 v = g.tiles[t];
+        id.c = v.x; id.inst = v.y; id.rt = v.z; id.sp = v.w;
+    } else {
+        id.c = 0; id.inst = 0;
+        id.rt = (int)(t / g.cls[0].splits);
+        id.sp = (int)(t % g.cls[0].splits);
+    }
+    return id;
+}
+
+template <class F, int C>
+__global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcGroup<C> g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t b_tile = (uint32_t)a.nc * 128u;
+    const uint32_t b_slot = (uint32_t)g.stage_nc * 128u;      // one part of the matrix tile
     const uint32_t a_bytes = F::kAParts * kATile;
-    const uint32_t stage_bytes = a_bytes + kBParts * b_tile;
-    uint64_t* bars = (uint64_t*)(smem + a.stages * stage_bytes);
+    const uint32_t stage_bytes = a_bytes + kBParts * b_slot;
+    uint64_t* bars = (uint64_t*)(smem + g.stages * stage_bytes);
     uint32_t* tmem_slot = (uint32_t*)(bars + kBars);
     auto full = [&](int s) { return tc::smem_u32(bars + s); };
     auto empty = [&](int s) { return tc::smem_u32(bars + kMaxStages + s); };
@@ -139,9 +167,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
     const uint32_t mma_done = tc::smem_u32(bars + 2 * kMaxStages + 8);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int stages = a.stages;
-    const int64_t ntiles = a.row_tiles * a.splits;
-    const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int stages = g.stages;
+    const int64_t my_tiles = blockIdx.x < g.ntiles ? (g.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < stages; ++s) {
@@ -171,59 +198,68 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             // ---- loader: both operands' parts by TMA ----
             int64_t issued_last[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) issued_last[s] = -1;
-            const int64_t total = my_tiles * a.nkb;
-            for (int64_t it = 0; it < total; ++it) {
-                const int s = (int)(it % stages);
-                if (it >= stages && !tc::mbar_wait(empty(s), (uint32_t)((it / stages) - 1) & 1, a.status)) break;
-                const int64_t t = blockIdx.x + (it / a.nkb) * gridDim.x;
-                const int kb = (int)(it % a.nkb);
-                const int row0 = (int)((t / a.splits) * kRows);
-                const int col0 = (int)(t % a.splits) * a.nc;
-                tc::mbar_arrive_expect_tx(full(s), a_bytes + kBParts * b_tile);
-                const uint32_t st = tc::smem_u32(smem + s * stage_bytes);
-                for (int q = 0; q < F::kAParts; ++q)
-                    tma_load_3d(st + q * kATile, &amap, kb * F::kBK, row0, q, full(s));
-                for (int part = 0; part < kBParts; ++part)   // rows col0.. of b0, b1, b2
-                    tma_load_3d(st + a_bytes + part * b_tile, &bmap, kb * F::kBK, col0, part, full(s));
-                issued_last[s] = it;
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t i = 0; i < my_tiles && ok; ++i) {
+                const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
+                const TcClass& k = g.cls[id.c];
+                const int row0 = id.inst * k.rows + id.rt * kRows;
+                const int col0 = id.inst * k.ncols + id.sp * k.nc;
+                const uint32_t b_tile = (uint32_t)k.nc * 128u;
+                for (int kb = 0; kb < k.nkb; ++kb, ++it) {
+                    const int s = (int)(it % stages);
+                    if (it >= stages && !tc::mbar_wait(empty(s), (uint32_t)((it / stages) - 1) & 1, g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_arrive_expect_tx(full(s), a_bytes + kBParts * b_tile);
+                    const uint32_t st = tc::smem_u32(smem + s * stage_bytes);
+                    for (int q = 0; q < F::kAParts; ++q)
+                        tma_load_3d(st + q * kATile, &k.xmap, kb * F::kBK, row0, q, full(s));
+                    for (int part = 0; part < kBParts; ++part)   // rows col0.. of b0, b1, b2
+                        tma_load_3d(st + a_bytes + part * b_slot, &k.mmap, kb * F::kBK, col0, part, full(s));
+                    issued_last[s] = it;
+                }
             }
             // never leave the CTA with copies in flight
             for (int s = 0; s < stages; ++s)
                 if (issued_last[s] >= 0)
-                    tc::mbar_wait(full(s), (uint32_t)(issued_last[s] / stages) & 1, a.status);
+                    tc::mbar_wait(full(s), (uint32_t)(issued_last[s] / stages) & 1, g.status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            const uint32_t id = idesc_of<F>(a.nc);
             int64_t it = 0;
             int64_t uses[2] = {0, 0};      // uses of each main slot so far
             bool ok = true;
             for (int64_t i = 0; i < my_tiles && ok; ++i) {
+                const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
+                const TcClass& k = g.cls[id.c];
+                const uint32_t idd = idesc_of<F>(k.nc);
                 const int b = (int)(i & 1);
-                if (i >= 2 && !tc::mbar_wait(cempty(b), (uint32_t)((i >> 1) - 1) & 1, a.status)) break;
-                const uint32_t corr = tmem + (uint32_t)((2 + b) * a.nc);
-                for (int kb = 0; kb < a.nkb; ++kb, ++it) {
+                if (i >= 2 && !tc::mbar_wait(cempty(b), (uint32_t)((i >> 1) - 1) & 1, g.status)) break;
+                const uint32_t corr = tmem + (uint32_t)((2 + b) * g.stage_nc);
+                for (int kb = 0; kb < k.nkb; ++kb, ++it) {
                     const int s = (int)(it % stages);
                     const int r = (int)(it & 1);
-                    if (uses[r] >= 1 && !tc::mbar_wait(mempty(r), (uint32_t)(uses[r] - 1) & 1, a.status)) {
+                    if (uses[r] >= 1 && !tc::mbar_wait(mempty(r), (uint32_t)(uses[r] - 1) & 1, g.status)) {
                         ok = false;
                         break;
                     }
                     ++uses[r];
-                    if (!tc::mbar_wait(full(s), (uint32_t)(it / stages) & 1, a.status)) { ok = false; break; }
+                    if (!tc::mbar_wait(full(s), (uint32_t)(it / stages) & 1, g.status)) { ok = false; break; }
                     tc::tc_fence_after();
-                    const uint32_t mainacc = tmem + (uint32_t)(r * a.nc);
+                    const uint32_t mainacc = tmem + (uint32_t)(r * g.stage_nc);
                     const uint32_t abase = tc::smem_u32(smem + s * stage_bytes);
                     const uint32_t bbase = abase + a_bytes;
 #pragma unroll 1
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint32_t ko = kk * 32;
-                        mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), id, kk != 0);
+                        mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), idd, kk != 0);
 #pragma unroll
                         for (int c = 0; c < F::kCorr; ++c)
                             mma<F>(corr, tc::desc_k_sw128(abase + F::corr_a(c) * kATile + ko),
-                                   tc::desc_k_sw128(bbase + F::corr_b(c) * b_tile + ko), id,
+                                   tc::desc_k_sw128(bbase + F::corr_b(c) * b_slot + ko), idd,
                                    (c == 0 && (kb | kk) == 0) ? 0u : 1u);
                     }
                     tc::mma_commit(empty(s));
@@ -233,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             }
             // every issued MMA has completed before TMEM can be released
             tc::mma_commit(mma_done);
-            tc::mbar_wait(mma_done, 0, a.status);
+            tc::mbar_wait(mma_done, 0, g.status);
         }
     } else {
         // ---- epilogue: lane quarter (warp mod 4), column quarter ((warp - 2) / 4) ----
@@ -241,22 +277,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
         const int cq = (warp - 2) >> 2;
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const int nch = a.nc / 16;                        // <= 8 chunks of 16 columns
-        const int c0 = 2 * cq, c1 = min(nch, 2 * cq + 2);
+        int64_t it = 0;
         for (int64_t i = 0; i < my_tiles; ++i) {
+            const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
+            const TcClass& k = g.cls[id.c];
+            const int nch = k.nc / 16;                        // <= 8 chunks of 16 columns
+            const int c0 = 2 * cq, c1 = min(nch, 2 * cq + 2);
             const int b = (int)(i & 1);
             float acc[kQuartCols];
 #pragma unroll
             for (int u = 0; u < kQuartCols; ++u) acc[u] = 0.f;
             bool ok = true;
             // main product, one K-block slot at a time, summed in FP32 registers
-            for (int kb = 0; kb < a.nkb && ok; ++kb) {
-                const int64_t it = i * a.nkb + kb;
+            for (int kb = 0; kb < k.nkb && ok; ++kb, ++it) {
                 const int rs = (int)(it & 1);
-                ok = __all_sync(0xffffffffu, tc::mbar_wait(mfull(rs), (uint32_t)(it >> 1) & 1, a.status));
+                ok = __all_sync(0xffffffffu, tc::mbar_wait(mfull(rs), (uint32_t)(it >> 1) & 1, g.status));
                 if (!ok) break;
                 tc::tc_fence_after();
-                const uint32_t slot = tmem + lane_off + (uint32_t)(rs * a.nc);
+                const uint32_t slot = tmem + lane_off + (uint32_t)(rs * g.stage_nc);
 #pragma unroll
                 for (int c = 0; c < kQuartCols / 16; ++c) {
                     if (c0 + c < c1) {          // warp-uniform
@@ -272,17 +310,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
                 if (lane == 0) tc::mbar_arrive(mempty(rs));
             }
             if (!ok) break;
-            ok = __all_sync(0xffffffffu, tc::mbar_wait(cfull(b), (uint32_t)(i >> 1) & 1, a.status));
+            ok = __all_sync(0xffffffffu, tc::mbar_wait(cfull(b), (uint32_t)(i >> 1) & 1, g.status));
             if (!ok) break;
             tc::tc_fence_after();
-            const int64_t t = blockIdx.x + i * gridDim.x;
-            const int64_t q = (t / a.splits) * kRows + r;
-            const int col0 = (int)(t % a.splits) * a.nc;
-            const bool valid = q < a.rows;
+            const int64_t q = (int64_t)id.rt * kRows + r;
+            const int col0 = id.sp * k.nc;
+            const bool valid = q < k.rows;
             // next-mode layout of output (q, i): position jq + p' (rq + (R / n') i)
             int64_t jq = 0, rq = 0;
-            if (!a.last) { jq = q % a.next_n; rq = q / a.next_n; }
-            const uint32_t cset = tmem + lane_off + (uint32_t)((2 + b) * a.nc);
+            if (!k.last) { jq = q % k.next_n; rq = q / k.next_n; }
+            const uint32_t cset = tmem + lane_off + (uint32_t)((2 + b) * g.stage_nc);
 #pragma unroll
             for (int c = 0; c < kQuartCols / 16; ++c) {    // y = corrections + main, in FP32
                 if (c0 + c < c1) {
@@ -298,21 +335,23 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(TcMode a, const __
             if (lane == 0) tc::mbar_arrive(cempty(b));      // corrections read: TMEM set free
             if (!valid) continue;
             // output column col of row q: next-mode position jq + p' (rq + (R / n') col)
-            // (or q + R col after the last mode); successive columns step by dpos
-            const int64_t dpos = a.last ? a.ldy : (int64_t)a.next_p * a.next_rows_per_i;
+            // (or q + ldy col for FP32); successive columns step by dpos
+            const int64_t dpos = k.last ? k.ldy : (int64_t)k.next_p * k.next_rows_per_i;
+            float* yb = k.last ? k.yout + (int64_t)id.inst * k.y_stride : nullptr;
+            const int64_t pbase = k.last ? 0 : (int64_t)id.inst * k.p_stride;
 #pragma unroll
             for (int c = 0; c < kQuartCols / 16; ++c) {
                 if (c0 + c >= c1) continue;
                 const int i0 = col0 + (c0 + c) * 16;
-                int64_t pos = a.last ? q + a.ldy * (int64_t)i0
-                                     : jq + (int64_t)a.next_p * (rq + a.next_rows_per_i * (int64_t)i0);
-                const int lim = min(16, a.ncols - i0);
+                int64_t pos = k.last ? q + k.ldy * (int64_t)i0
+                                     : pbase + jq + (int64_t)k.next_p * (rq + k.next_rows_per_i * (int64_t)i0);
+                const int lim = min(16, k.ncols - i0);
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     if (u >= lim) break;
                     const float y = acc[c * 16 + u];
-                    if (a.last) a.yout[pos] = a.accum ? a.yout[pos] + y : y;
-                    else store_parts<F>(a.pout, a.out_part_pitch, pos, y, 0.f);
+                    if (k.last) yb[pos] = k.accum ? yb[pos] + y : y;
+                    else store_parts<F>(k.pout, k.out_part_pitch, pos, y, 0.f);
                     pos += dpos;
                 }
             }
@@ -371,41 +410,52 @@ __global__ void __launch_bounds__(256) split_matrix_kernel(const double* __restr
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Geometry {
-    int nkb, nc, splits, stages;
-    size_t smem;
+    int nc, splits;
 };
 
-// Output columns per CTA tile (nc <= 128, one MMA) and pipeline depth.  Among the
-// column splittings with nc a multiple of 16, take the one whose tile waves over
-// the SMs cost least, a tile costing its columns plus a fixed 32-column-equivalent
-// overhead (the operand tile re-read, the epilogue's fixed work).
-template <class F>
-int geometry(int K, int ncols, int64_t rows, Geometry* g) {
-    if (K < 1 || ncols < 1 || rows < 1) return MM_ERR_SHAPE;
+// Columns per CTA tile given at most nc_cap (a multiple of 16, <= 128): the fewest
+// splits, then the narrowest multiple of 16 that covers the columns.
+Geometry split_cols(int ncols, int nc_cap) {
+    const int n16 = round_up(ncols, 16);
+    Geometry g;
+    g.splits = (n16 + nc_cap - 1) / nc_cap;
+    g.nc = round_up((n16 + g.splits - 1) / g.splits, 16);
+    g.splits = (n16 + g.nc - 1) / g.nc;
+    return g;
+}
+
+// One product alone on the GPU: among the column splittings, take the one whose
+// tile waves over the SMs cost least, a tile costing its columns plus a fixed
+// 32-column-equivalent overhead (the operand tile re-read, the epilogue's fixed work).
+Geometry geometry_single(int ncols, int64_t rows) {
     const int n16 = round_up(ncols, 16);
     const int64_t row_tiles = (rows + kRows - 1) / kRows;
     const int64_t sms = num_sms();
     const int s_min = (n16 + kNcMax - 1) / kNcMax;
-    int64_t best = -1;
+    Geometry best{};
+    int64_t best_cost = -1;
     for (int sp = s_min; sp <= 2 * s_min && sp <= n16 / 16; ++sp) {
-        const int nc = round_up((n16 + sp - 1) / sp, 16);
-        const int splits = (n16 + nc - 1) / nc;
-        const int64_t waves = (row_tiles * splits + sms - 1) / sms;
-        const int64_t cost = waves * (nc + 32);
-        if (best < 0 || cost < best) {
-            best = cost;
-            g->nc = nc;
-            g->splits = splits;
+        const Geometry g = split_cols(ncols, round_up((n16 + sp - 1) / sp, 16));
+        const int64_t waves = (row_tiles * g.splits + sms - 1) / sms;
+        const int64_t cost = waves * (g.nc + 32);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = g;
         }
     }
-    g->nkb = (K + F::kBK - 1) / F::kBK;
-    const size_t stage = (size_t)F::kAParts * kATile + kBParts * (size_t)g->nc * 128;
+    return best;
+}
+
+// Pipeline depth and dynamic shared memory for tiles up to stage_nc columns.
+template <class F>
+int stages_for(int stage_nc, int* stages, size_t* smem) {
+    const size_t stage = (size_t)F::kAParts * kATile + kBParts * (size_t)stage_nc * 128;
     const size_t fixed = 1024 + kBars * 8 + 16;
     int st = (int)((kSmemLimit - fixed) / stage);
     st = std::min(st, kMaxStages);
     if (st < 2) return MM_ERR_UNSUPPORTED;
-    g->stages = st;
-    g->smem = fixed + st * stage;
+    *stages = st;
+    *smem = fixed + st * stage;
     return MM_OK;
 }
 
@@ -449,37 +499,86 @@ int encode_parts(CUtensorMap* map, const PartView& v, int nparts, int box_rows) 
 }
 
 template <class F>
-int launch_form(const PartView& X, const PartView& M, const TcOut& o, unsigned int* status, cudaStream_t s) {
+int fill_class(TcClass& k, const TcClassSpec& c, const Geometry& geo) {
+    if (c.X.n != c.M.n || c.count < 1 || c.rows < 1 || c.ncols < 1) return MM_ERR_SHAPE;
+    if ((int64_t)c.rows * c.count > 0x7fffffffLL || (int64_t)c.ncols * c.count > 0x7fffffffLL)
+        return MM_ERR_SHAPE;
+    k.k = c.X.n;
+    k.ncols = c.ncols;
+    k.nkb = (c.X.n + F::kBK - 1) / F::kBK;
+    k.nc = geo.nc;
+    k.splits = geo.splits;
+    k.rows = c.rows;
+    k.last = c.out.last;
+    k.accum = c.out.accum;
+    k.yout = c.out.y;
+    k.ldy = c.out.ldy;
+    k.y_stride = c.y_stride;
+    k.pout = c.out.parts;
+    k.out_part_pitch = c.out.part_pitch;
+    k.p_stride = c.p_stride;
+    k.next_n = c.out.next_n;
+    k.next_p = c.out.next_p;
+    k.next_rows_per_i = c.out.next_rows_per_i;
+    if (!k.last && (k.next_n < 1 || k.next_p < k.next_n)) return MM_ERR_ARG;
+    int rc = encode_parts<F>(&k.xmap, c.X, F::kAParts, kRows);
+    if (!rc) rc = encode_parts<F>(&k.mmap, c.M, kBParts, geo.nc);
+    return rc;
+}
+
+template <class F, int C>
+int launch_group(TcGroup<C>& g, int64_t ctas, cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        MM_CUDA_TRY(cudaFuncSetAttribute(tc_mode_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        MM_CUDA_TRY(cudaFuncSetAttribute(tc_mode_kernel<F, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemLimit));
         configured = true;
     }
-    if (X.n != M.n || X.rows > 0x7fffffffLL || M.rows > 0x7fffffffLL) return MM_ERR_SHAPE;
-    Geometry g;
-    int rc = geometry<F>(X.n, (int)M.rows, X.rows, &g);
+    int stages;
+    size_t smem;
+    int rc = stages_for<F>(g.stage_nc, &stages, &smem);
     if (rc) return rc;
-    TcMode m{};
-    m.k = X.n; m.ncols = (int)M.rows;
-    m.nkb = g.nkb; m.nc = g.nc; m.splits = g.splits; m.stages = g.stages;
-    m.rows = X.rows;
-    m.row_tiles = (X.rows + kRows - 1) / kRows;
-    m.last = o.last; m.accum = o.accum;
-    m.yout = o.y; m.ldy = o.ldy;
-    m.pout = o.parts; m.out_part_pitch = o.part_pitch;
-    m.next_n = o.next_n; m.next_p = o.next_p; m.next_rows_per_i = o.next_rows_per_i;
-    m.status = status;
-    if (!m.last && (m.next_n < 1 || m.next_p < m.next_n)) return MM_ERR_ARG;
-    CUtensorMap amap, bmap;
-    if ((rc = encode_parts<F>(&amap, X, F::kAParts, kRows))) return rc;
-    if ((rc = encode_parts<F>(&bmap, M, kBParts, g.nc))) return rc;
-    const int64_t tiles = m.row_tiles * g.splits;
-    const int64_t ctas = std::min<int64_t>(tiles, num_sms());
+    g.stages = stages;
+    if (ctas < 1) return MM_OK;
     TraceScope tr(KC_CONTRACT_TF32, s);
-    tc_mode_kernel<F><<<(unsigned)ctas, kThreads, g.smem, s>>>(m, amap, bmap);
+    tc_mode_kernel<F, C><<<(unsigned)ctas, kThreads, smem, s>>>(g);
     MM_LAUNCH_CHECK();
     return MM_OK;
+}
+
+template <class F>
+int launch_single(const PartView& X, const PartView& M, const TcOut& o, unsigned int* status, cudaStream_t s) {
+    if (X.n != M.n || X.rows > 0x7fffffffLL || M.rows > 0x7fffffffLL) return MM_ERR_SHAPE;
+    TcClassSpec c{};
+    c.X = X; c.rows = (int)X.rows; c.M = M; c.ncols = (int)M.rows; c.count = 1; c.out = o;
+    const Geometry geo = geometry_single(c.ncols, X.rows);
+    TcGroup<1> g{};
+    int rc = fill_class<F>(g.cls[0], c, geo);
+    if (rc) return rc;
+    g.tiles = nullptr;
+    g.ntiles = ((X.rows + kRows - 1) / kRows) * geo.splits;
+    g.stage_nc = geo.nc;
+    g.status = status;
+    return launch_group<F, 1>(g, std::min<int64_t>(g.ntiles, num_sms()), s);
+}
+
+template <class F>
+int launch_grouped(const TcClassSpec* cls, int ncls, const int* nc_cap, const int4* tiles, int64_t ntiles,
+                   unsigned int* status, cudaStream_t s) {
+    if (ncls < 1 || ncls > kMaxClasses) return MM_ERR_ARG;
+    TcGroup<kMaxClasses> g{};            // the kernel parameters (~12 KB)
+    int stage_nc = 16;
+    for (int c = 0; c < ncls; ++c) {
+        const Geometry geo = split_cols(cls[c].ncols, nc_cap[c]);
+        int rc = fill_class<F>(g.cls[c], cls[c], geo);
+        if (rc) return rc;
+        stage_nc = std::max(stage_nc, geo.nc);
+    }
+    g.tiles = tiles;
+    g.ntiles = ntiles;
+    g.stage_nc = stage_nc;
+    g.status = status;
+    return launch_group<F, kMaxClasses>(g, std::min<int64_t>(ntiles, num_sms()), s);
 }
 
 }  // namespace
@@ -527,8 +626,36 @@ int split_matrix(int prec, const double* src, int64_t ld, int colmajor, int zero
 
 int tc_product(int prec, const PartView& X, const PartView& M, const TcOut& o, unsigned int* status,
                cudaStream_t s) {
-    if (prec == MM_BF16X3) return launch_form<FormBF16>(X, M, o, status, s);
-    return launch_form<FormTF32>(X, M, o, status, s);
+    if (prec == MM_BF16X3) return launch_single<FormBF16>(X, M, o, status, s);
+    return launch_single<FormTF32>(X, M, o, status, s);
+}
+
+int tc_group_tiles(int prec, const TcClassSpec* cls, int ncls, const int* nc_cap, std::vector<int4>& tiles) {
+    if (ncls < 1 || ncls > kMaxClasses) return MM_ERR_ARG;
+    const int bk = prec == MM_BF16X3 ? FormBF16::kBK : FormTF32::kBK;
+    std::vector<std::pair<int64_t, int4>> v;
+    for (int c = 0; c < ncls; ++c) {
+        const Geometry geo = split_cols(cls[c].ncols, nc_cap[c]);
+        const int nkb = (cls[c].X.n + bk - 1) / bk;
+        const int rt = (cls[c].rows + kRows - 1) / kRows;
+        const int64_t cost = (int64_t)nkb * (geo.nc + 32);
+        for (int j = 0; j < cls[c].count; ++j)
+            for (int r = 0; r < rt; ++r)
+                for (int sp = 0; sp < geo.splits; ++sp) v.push_back({cost, make_int4(c, j, r, sp)});
+    }
+    // decreasing cost; the CTAs take tiles round-robin from the front
+    std::stable_sort(v.begin(), v.end(), [](const std::pair<int64_t, int4>& a, const std::pair<int64_t, int4>& b) {
+        return a.first > b.first;
+    });
+    tiles.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) tiles[i] = v[i].second;
+    return MM_OK;
+}
+
+int tc_group_product(int prec, const TcClassSpec* cls, int ncls, const int* nc_cap, const int4* dev_tiles,
+                     int64_t ntiles, unsigned int* status, cudaStream_t s) {
+    if (prec == MM_BF16X3) return launch_grouped<FormBF16>(cls, ncls, nc_cap, dev_tiles, ntiles, status, s);
+    return launch_grouped<FormTF32>(cls, ncls, nc_cap, dev_tiles, ntiles, status, s);
 }
 
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s) {

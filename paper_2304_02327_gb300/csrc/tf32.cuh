@@ -2,6 +2,8 @@
 // steppers (expint_mixed.cu).
 #pragma once
 
+#include <vector>
+
 #include "plan.cuh"
 
 namespace mm {
@@ -49,6 +51,27 @@ struct TcOut {
 // both with the contraction index fastest (X.n == M.n).
 int tc_product(int prec, const PartView& X, const PartView& M, const TcOut& out, unsigned int* status,
                cudaStream_t s);
+
+// Grouped products: up to MM_TC_MAX_CLASSES classes of `count` equal-shape
+// instances each, operands packed instance after instance (X rows j * rows..,
+// M rows j * ncols..), outputs at per-instance strides (y_stride floats for FP32,
+// p_stride elements within each part for split output).
+#define MM_TC_MAX_CLASSES 32
+struct TcClassSpec {
+    PartView X;             // rows = rows * count
+    int rows;
+    PartView M;             // rows = ncols * count
+    int ncols;
+    int count;
+    TcOut out;
+    int64_t y_stride, p_stride;
+};
+// The tile list of a grouped product, tiles of decreasing cost (nc per class from
+// nc_cap[c], a multiple of 16 <= 128).
+int tc_group_tiles(int prec, const TcClassSpec* cls, int ncls, const int* nc_cap, std::vector<int4>& tiles);
+// One persistent launch over the tiles (device array of tc_group_tiles' output).
+int tc_group_product(int prec, const TcClassSpec* cls, int ncls, const int* nc_cap, const int4* dev_tiles,
+                     int64_t ntiles, unsigned int* status, cudaStream_t s);
 
 // Mode mu with phi_ell: reads operand `in`, writes the next mode's operand parts to
 // out_parts (mu < d) or the FP32 result in natural order to yout (mu == d).

@@ -18,12 +18,17 @@ size_t g_used = 0;
 
 }  // namespace
 
+void trace_count(int cls, long long n) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_launches[cls] += n;
+}
+
 TraceScope::TraceScope(int cls, cudaStream_t s) : cls_(cls), s_(s), slot_(-1) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lk(g_mu);
     g_launches[cls]++;
     if (!g_on) return;
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     if (g_used == g_pool.size()) {
         Pair p{};
         if (cudaEventCreate(&p.a) != cudaSuccess) return;

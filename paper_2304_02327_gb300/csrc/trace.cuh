@@ -14,8 +14,12 @@ enum KernelClass : int {
     KC_COUNT = MM_KC_COUNT,
 };
 
-// RAII: counts one launch of class `cls` and, if tracing is on and the stream is
-// not being captured, brackets it with a pair of events.
+// RAII: counts one launch of class `cls` and, if tracing is on, brackets it with a
+// pair of events; launches into a stream under capture are neither counted nor
+// timed (their graph's launches are counted with trace_count).
+// Adds n launches of class cls that ran inside a CUDA graph (counted, not timed).
+void trace_count(int cls, long long n);
+
 class TraceScope {
 public:
     TraceScope(int cls, cudaStream_t s);

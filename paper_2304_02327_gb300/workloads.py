@@ -231,7 +231,19 @@ def workload(name: str, **over) -> Problem:
         "riccati_n2048_expeuler": lambda: riccati_2d(2048, 5, 1e-4, 50, EXPEULER),
         "riccati_n2048_etd2rk": lambda: riccati_2d(2048, 5, 1e-4, 50, ETD2RK),
     }
+    if name in BATCHED:
+        raise ValueError(f"{name} is a batch: use batched_workload()")
     p = table[name]()
     for k, v in over.items():
         setattr(p, k, v)
     return p
+
+
+# Batches of independent problems, named by what they are.
+BATCHED = {
+    "batch_ac2d_1024_expeuler": lambda: batched_allen_cahn(1024, 4, 1e-3, 20),
+}
+
+
+def batched_workload(name: str) -> List[Problem]:
+    return BATCHED[name]()

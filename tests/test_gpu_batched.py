@@ -1,0 +1,127 @@
+"""Parity of the batched mixed-form stepper (many independent 2D problems of uneven
+size in one graph-captured run) with the FP64 oracle, instance by instance, and with
+the single-problem mixed path.
+
+The batched prepass performs the single-problem mixed prepass's arithmetic and the
+grouped tensor-core launch computes every output element with the same sequence of
+tensor-core products (K-blocks in order, the main product summed in registers), so
+a batch must reproduce the single-problem path bit for bit, whatever the tiling.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.integrators import OracleProblem, integrate, rel_err_inf, rel_err_fro
+from paper_2304_02327_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-6
+FORMS = ["tf32x3", "bf16x3"]
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2304_02327_gb300 import api as _api, build
+    build.build()
+    _api.lib()
+    return _api
+
+
+@pytest.fixture(params=FORMS)
+def form(request):
+    return request.param
+
+
+def small_batch(steps=20):
+    """A dozen Allen-Cahn instances: several sizes (two equal, so a class holds more
+    than one instance), one non-square, eps log-uniform."""
+    probs = wl.batched_allen_cahn(count=10, seed=11, steps=steps,
+                                  sizes=(48, 64, 96, 128, 160, 208, 256))
+    rng = np.random.default_rng(3)
+    A1, A2 = wl.fd_matrix(72, 0.02), wl.fd_matrix(136, 0.02)
+    probs.append(wl.Problem(name="ac_nonsquare", A=[A1, A2], u0=rng.uniform(-0.9, 0.9, (136, 72)),
+                            g_kind=wl.G_CUBIC, cubic=(0.0, 1.0, 0.0, -1.0), tau=1e-3, steps=steps,
+                            scheme=wl.EXPEULER))
+    probs.append(probs[2].__class__(**{**probs[2].__dict__, "name": "dup", "u0": -probs[2].u0}))
+    return probs
+
+
+def run_batch(api, probs, form, steps, **kw):
+    plans, gs, Us = api.setup_batch(probs, form)
+    b = api.Batch(plans, gs, Us, **kw)
+    b.run(steps)
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    return [u.cpu().numpy() for u in Us], b
+
+
+def test_batch_matches_oracle_per_instance(api, form):
+    probs = small_batch()
+    got, b = run_batch(api, probs, form, 20)
+    assert b.info()["classes"] == len({p.u0.shape for p in probs})
+    for p, g in zip(probs, got):
+        ref = integrate(OracleProblem.from_problem(p, lmax=1), p.u0, p.scheme, p.steps)
+        assert rel_err_inf(g, ref) <= TOL_STEP and rel_err_fro(g, ref) <= TOL_STEP, p.name
+
+
+@pytest.mark.parametrize("nc_cap", [128, 64, 48])
+def test_batch_equals_single_problem_path_bitwise(api, form, nc_cap):
+    probs = small_batch(steps=5)
+    got, _ = run_batch(api, probs, form, 5, autotune=False, nc_cap=nc_cap)
+    for p, g in zip(probs, got):
+        plan, gg, U = api.setup(p, form)
+        api.expint_step(plan, p.scheme, U, 5, g=gg)
+        np.testing.assert_array_equal(g, U.cpu().numpy(), err_msg=p.name)
+
+
+def test_batch_graph_and_plain_launches_agree(api, form):
+    probs = small_batch(steps=4)
+    g1, b1 = run_batch(api, probs, form, 4, graph=True)
+    g2, b2 = run_batch(api, probs, form, 4, graph=False)
+    for a, c in zip(g1, g2):
+        np.testing.assert_array_equal(a, c)
+    # a second run of the captured graph continues from the updated states
+    b1.run(4)
+    torch.cuda.synchronize()
+    b2.run(4)
+    torch.cuda.synchronize()
+    for a, c in zip(b1.Us, b2.Us):
+        assert torch.equal(a, c)
+
+
+def test_batch_autotune_picks_a_candidate(api, form):
+    probs = small_batch(steps=2)
+    _, b = run_batch(api, probs, form, 2, autotune=True)
+    assert b.info()["nc_cap"] in (128, 96, 64)
+
+
+def test_batch_rejects_unsupported(api):
+    p = small_batch(steps=1)[:2]
+    plans, gs, Us = api.setup_batch(p, "fp64")
+    with pytest.raises(api.PhisplitError) as e:
+        api.Batch(plans, gs, Us)
+    assert e.value.code == -3
+    plans, gs, Us = api.setup_batch(p, "bf16x3")
+    with pytest.raises(api.PhisplitError):
+        api.Batch(plans, gs, Us, scheme=wl.ETD2RK)
+
+
+def test_batch_full_config_sampled_instances(api):
+    """1024 instances, n uniform over {48, 64, ..., 512}, eps log-uniform in
+    [1e-3, 1e-1], 20 exponential Euler steps in BF16x3 with the autotuned tiling and
+    the captured graph (the configuration the bench times); eight instances,
+    including the largest and the smallest size, are integrated by the oracle."""
+    probs = wl.batched_allen_cahn()
+    got, b = run_batch(api, probs, "bf16x3", 20)
+    assert b.info()["dof"] == sum(p.u0.size for p in probs)
+    rng = np.random.default_rng(2024)
+    sizes = np.array([p.n[0] for p in probs])
+    pick = set(rng.choice(len(probs), 6, replace=False).tolist())
+    pick |= {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    for k in sorted(pick):
+        p = probs[k]
+        ref = integrate(OracleProblem.from_problem(p, lmax=1), p.u0, p.scheme, p.steps)
+        assert rel_err_inf(got[k], ref) <= TOL_STEP, (k, p.n[0])
