@@ -536,6 +536,9 @@ def ours(args):
         "e2e": {"value": e2e_value, "unit": METRIC, "steps": e2e_steps,
                 "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
         "gpu_launches": total_launches,
+        "kernel_ms_per_step": {"contract": k_ms / args.steps,
+                               "prepass": launches[api.KC_PREPASS][1] / args.steps,
+                               "split_update": launches[api.KC_SPLIT][1] / args.steps},
         "launches_by_kernel": {"contract_fp64": launches[api.KC_CONTRACT_FP64][0],
                                "contract_tf32": launches[api.KC_CONTRACT_TF32][0],
                                "prepass": launches[api.KC_PREPASS][0],

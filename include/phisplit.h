@@ -101,7 +101,7 @@ typedef struct mm_plan_s* mm_plan;
 
 /*
  * phi_plan_create -- form phi_l(tau A_mu), l = 0..ell_max, for every direction
- * (Section 3.1: scaling so that ||tau A / 2^s||_1 <= 1/2, a truncated Taylor
+ * (Section 3.1: scaling so that ||tau A / 2^s||_1 <= 1, a truncated Taylor
  * series of phi_ell_max at the scaled matrix, phi_{l-1}(X) = X phi_l(X) + I/(l-1)!,
  * then s applications of the squaring recurrence eq. (16)), all in FP64 on the
  * GPU.  Directions whose A_mu are bitwise equal share one set of phi matrices.

@@ -47,42 +47,75 @@ struct BInst {                         // device table, one entry per instance
 
 // W = K u + g(t, u) in parts, the stencil from differences of the double-float
 // split of the state (the arithmetic of the single-problem mixed prepass, d = 2).
+// A 32 x 32 tile of one instance and its one-element halo are split once into
+// shared memory (each state value read and split ~1.1 times instead of five);
+// 256 threads, four rows each.  Tiles are numbered instance after instance
+// (tile_begin holds each instance's first tile) and each block takes one
+// contiguous range, so it locates its instance once and then walks forward.
+constexpr int kT = 32;
+
 __global__ void __launch_bounds__(256) batch_prepass_kernel(const BInst* __restrict__ tab,
-                                                            const int4* __restrict__ chunks, int64_t nchunks,
-                                                            float t, int prec) {
-    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int4 ch = chunks[c];
-        const BInst& b = tab[ch.x];
+                                                            const int64_t* __restrict__ tile_begin, int count,
+                                                            int64_t ntiles, float t, int prec) {
+    __shared__ float2 sp[kT + 2][kT + 2];
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t T0 = blockIdx.x * per, T1 = min(ntiles, T0 + per);
+    if (T0 >= T1) return;
+    int inst = 0, hi = count;                   // tile_begin[inst] <= T0 < tile_begin[hi]
+    while (hi - inst > 1) {
+        const int mid = (inst + hi) >> 1;
+        if (__ldg(tile_begin + mid) <= T0) inst = mid;
+        else hi = mid;
+    }
+    int64_t next = __ldg(tile_begin + inst + 1);
+    for (int64_t T = T0; T < T1; ++T) {
+        while (T >= next) next = __ldg(tile_begin + (++inst) + 1);
+        const BInst b = tab[inst];      // by value: the stores below cannot alias it
         const double* U = b.U;
         const int n1 = b.n1, n2 = b.n2;
-        for (int e = threadIdx.x; e < ch.z; e += blockDim.x) {
-            const int i = ch.y + e;
-            const int i1 = i % n1, i2 = i / n1;
-            float uh, ul;
-            mx::d2ff(__ldg(U + i), uh, ul);
+        const int tiles1 = (n1 + kT - 1) / kT;
+        const int lt = (int)(T - __ldg(tile_begin + inst));
+        const int a1 = (lt % tiles1) * kT, a2 = (lt / tiles1) * kT;
+        for (int e = threadIdx.x; e < (kT + 2) * (kT + 2); e += blockDim.x) {
+            const int r = e / (kT + 2), c = e % (kT + 2);
+            const int i1 = a1 - 1 + c, i2 = a2 - 1 + r;
+            float2 v = make_float2(0.f, 0.f);
+            if (i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2) mx::d2ff(__ldg(U + i1 + (int64_t)n1 * i2), v.x, v.y);
+            sp[r][c] = v;
+        }
+        __syncthreads();
+        const int c = threadIdx.x % kT;
+        const int i1 = a1 + c;
+#pragma unroll
+        for (int q = 0; q < kT / 8; ++q) {
+            const int r = threadIdx.x / kT + 8 * q;
+            const int i2 = a2 + r;
+            if (i1 >= n1 || i2 >= n2) continue;
+            const float uh = sp[r + 1][c + 1].x, ul = sp[r + 1][c + 1].y;
             const float u = uh + ul;
+            const int i = i1 + n1 * i2;
             float acc = mx::g32(b.g, u, t, i);
-            float vh, vl;
             acc = fmaf(b.coef1[2 * n1 + i1], u, acc);
             if (i1 > 0) {
-                mx::d2ff(__ldg(U + i - 1), vh, vl);
-                acc = fmaf(b.coef1[i1], (vh - uh) + (vl - ul), acc);
+                const float2 v = sp[r + 1][c];
+                acc = fmaf(b.coef1[i1], (v.x - uh) + (v.y - ul), acc);
             }
             if (i1 + 1 < n1) {
-                mx::d2ff(__ldg(U + i + 1), vh, vl);
-                acc = fmaf(b.coef1[n1 + i1], (vh - uh) + (vl - ul), acc);
+                const float2 v = sp[r + 1][c + 2];
+                acc = fmaf(b.coef1[n1 + i1], (v.x - uh) + (v.y - ul), acc);
             }
             acc = fmaf(b.coef2[2 * n2 + i2], u, acc);
             if (i2 > 0) {
-                mx::d2ff(__ldg(U + i - n1), vh, vl);
-                acc = fmaf(b.coef2[i2], (vh - uh) + (vl - ul), acc);
+                const float2 v = sp[r][c + 1];
+                acc = fmaf(b.coef2[i2], (v.x - uh) + (v.y - ul), acc);
             }
             if (i2 + 1 < n2) {
-                mx::d2ff(__ldg(U + i + n1), vh, vl);
-                acc = fmaf(b.coef2[n2 + i2], (vh - uh) + (vl - ul), acc);
+                const float2 v = sp[r + 2][c + 1];
+                acc = fmaf(b.coef2[n2 + i2], (v.x - uh) + (v.y - ul), acc);
             }
             store_parts_prec(prec, b.wbase, b.w_part_pitch, b.w_off + i1 + (int64_t)b.p1 * i2, acc, 0.f);
         }
+        __syncthreads();
     }
 }
 
@@ -92,13 +125,17 @@ __global__ void __launch_bounds__(256) batch_update_kernel(const BInst* __restri
                                                            unsigned int* status) {
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int4 ch = chunks[c];
-        const BInst& b = tab[ch.x];
+        double* U = tab[ch.x].U;        // loaded once: the stores to U cannot alias them
+        const float* y = tab[ch.x].y;
+        const double tau = tab[ch.x].tau;
+        bool bad = false;
         for (int e = threadIdx.x; e < ch.z; e += blockDim.x) {
             const int i = ch.y + e;
-            const double v = fma(b.tau, mx::f2d(__ldg(b.y + i)), b.U[i]);
-            if (!mx::finite_bits(v)) atomicOr(status, MM_STATUS_NONFINITE);
-            b.U[i] = v;
+            const double v = fma(tau, mx::f2d(__ldg(y + i)), U[i]);
+            bad |= !mx::finite_bits(v);
+            U[i] = v;
         }
+        if (bad) atomicOr(status, MM_STATUS_NONFINITE);
     }
 }
 
@@ -129,8 +166,10 @@ struct mm_batch_s {
     };
     std::vector<Launch> launches;
     BInst* tab = nullptr;
-    int4* chunks = nullptr;
+    int4* chunks = nullptr;                 // update pass: {instance, start, length}
     int64_t nchunks = 0;
+    int64_t* tile_begin = nullptr;          // prepass: first 32 x 32 tile of each instance
+    int64_t ntiles = 0;
     unsigned int* status = nullptr;
     int use_graph = 1;
     cudaStream_t cap = nullptr;            // capture stream of the step graph
@@ -182,12 +221,18 @@ int tucker_modes(mm_batch_s* b, cudaStream_t s) {
 
 int64_t ew_grid(const mm_batch_s* b) { return std::min<int64_t>(b->nchunks, (int64_t)num_sms() * 8); }
 
+int prepass(mm_batch_s* b, double t, cudaStream_t s) {
+    const int64_t grid = std::min<int64_t>(b->ntiles, (int64_t)num_sms() * 8);
+    TraceScope tr(KC_PREPASS, s);
+    batch_prepass_kernel<<<(unsigned)grid, 256, 0, s>>>(b->tab, b->tile_begin, b->count, b->ntiles, (float)t,
+                                                         b->prec);
+    MM_LAUNCH_CHECK();
+    return MM_OK;
+}
+
 int one_step(mm_batch_s* b, double t, cudaStream_t s) {
-    {
-        TraceScope tr(KC_PREPASS, s);
-        batch_prepass_kernel<<<(unsigned)ew_grid(b), 256, 0, s>>>(b->tab, b->chunks, b->nchunks, (float)t, b->prec);
-        MM_LAUNCH_CHECK();
-    }
+    int rc0 = prepass(b, t, s);
+    if (rc0) return rc0;
     int rc = tucker_modes(b, s);
     if (rc) return rc;
     TraceScope tr(KC_SPLIT, s);
@@ -412,6 +457,19 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
         b->launches.push_back(L);
     }
     b->nchunks = (int64_t)chunks.size();
+    {
+        std::vector<int64_t> tb(count + 1, 0);
+        for (int j = 0; j < count; ++j)
+            tb[j + 1] = tb[j] + ((n1[j] + kT - 1) / kT) * ((n2[j] + kT - 1) / kT);
+        b->ntiles = tb[count];
+        if (!b->alloc((void**)&b->tile_begin, tb.size() * sizeof(int64_t)) ||
+            cudaMemcpyAsync(b->tile_begin, tb.data(), tb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = MM_ERR_NOMEM;
+            goto fail;
+        }
+    }
     if (!b->alloc((void**)&b->tab, tab.size() * sizeof(BInst)) ||
         !b->alloc((void**)&b->chunks, chunks.size() * sizeof(int4)) ||
         !b->alloc((void**)&b->status, sizeof(unsigned int))) {
@@ -436,11 +494,8 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
     }
     if (tune && tune->autotune && !tune->nc_cap) {
         // W from the initial states so the timed products see real operands
-        {
-            TraceScope tr(KC_PREPASS, s);
-            batch_prepass_kernel<<<(unsigned)ew_grid(b), 256, 0, s>>>(b->tab, b->chunks, b->nchunks, 0.f, prec);
-            if (cudaGetLastError() != cudaSuccess) { rc = MM_ERR_CUDA; goto fail; }
-        }
+        rc = prepass(b, 0.0, s);
+        if (rc) goto fail;
         rc = autotune(b, s);
         if (rc) goto fail;
     }

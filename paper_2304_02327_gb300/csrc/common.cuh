@@ -130,6 +130,7 @@ struct Gemm {
     const double* B; int64_t ldb, sB;
     int64_t ldc, sC;
     int b_kcontig;
+    int two_level;      // sum each K-tile's chain apart (plan-time products)
 };
 
 int num_sms();

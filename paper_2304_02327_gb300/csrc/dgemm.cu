@@ -17,7 +17,10 @@ namespace mm {
 
 namespace {
 
-template <int BM, int BN, int BK, int TM, int TN>
+// TWO: two-level summation -- each K-tile's FMA chain (BK terms) is added into a
+// separate total, so rounding grows with BK + K/BK instead of K (the plan's
+// squaring products, whose errors the squarings amplify).
+template <int BM, int BN, int BK, int TM, int TN, bool TWO>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 dgemm_kernel(Gemm g, Epi e, int tilesM, int tilesN) {
     constexpr int TX = BM / TM;
@@ -36,11 +39,17 @@ dgemm_kernel(Gemm g, Epi e, int tilesM, int tilesN) {
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
 
-    double acc[TM][TN];
+    double acc[TM][TN], tot[TWO ? TM : 1][TWO ? TN : 1];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    if (TWO) {
+#pragma unroll
+        for (int i = 0; i < (TWO ? TM : 1); ++i)
+#pragma unroll
+            for (int j = 0; j < (TWO ? TN : 1); ++j) tot[i][j] = 0.0;
+    }
 
     for (int k0 = 0; k0 < g.K; k0 += BK) {
 #pragma unroll
@@ -80,7 +89,22 @@ dgemm_kernel(Gemm g, Epi e, int tilesM, int tilesN) {
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
+        if (TWO) {
+#pragma unroll
+            for (int i = 0; i < (TWO ? TM : 1); ++i)
+#pragma unroll
+                for (int j = 0; j < (TWO ? TN : 1); ++j) {
+                    tot[i][j] += acc[i][j];
+                    acc[i][j] = 0.0;
+                }
+        }
         __syncthreads();
+    }
+    if (TWO) {
+#pragma unroll
+        for (int i = 0; i < (TWO ? TM : 1); ++i)
+#pragma unroll
+            for (int j = 0; j < (TWO ? TN : 1); ++j) acc[i][j] = tot[i][j];
     }
 
 #pragma unroll
@@ -97,14 +121,14 @@ dgemm_kernel(Gemm g, Epi e, int tilesM, int tilesN) {
     }
 }
 
-template <int BM, int BN, int BK, int TM, int TN>
+template <int BM, int BN, int BK, int TM, int TN, bool TWO>
 int launch_cfg(const Gemm& g, const Epi& e, cudaStream_t s) {
     int tilesM = (g.M + BM - 1) / BM, tilesN = (g.N + BN - 1) / BN;
     int64_t ntiles = (int64_t)tilesM * tilesN * g.batch;
     if (ntiles <= 0) return MM_OK;
     if (ntiles > 0x7fffffffLL) return MM_ERR_SHAPE;
     TraceScope tr(KC_CONTRACT_FP64, s);
-    dgemm_kernel<BM, BN, BK, TM, TN><<<(unsigned)ntiles, (BM / TM) * (BN / TN), 0, s>>>(g, e, tilesM, tilesN);
+    dgemm_kernel<BM, BN, BK, TM, TN, TWO><<<(unsigned)ntiles, (BM / TM) * (BN / TN), 0, s>>>(g, e, tilesM, tilesN);
     MM_LAUNCH_CHECK();
     return MM_OK;
 }
@@ -131,9 +155,14 @@ int launch_dgemm(const Gemm& g, const Epi& e, cudaStream_t s) {
     const int64_t sms = num_sms();
     // Largest tile whose grid still fills the machine several times; smaller
     // tiles trade operand reuse (irrelevant when DFMA-bound) for balance.
-    if (tiles_of(g, 64, 64) >= 6 * sms) return launch_cfg<64, 64, 16, 4, 4>(g, e, s);
-    if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 2, 2>(g, e, s);
-    return launch_cfg<16, 16, 16, 1, 1>(g, e, s);
+    if (g.two_level) {
+        if (tiles_of(g, 64, 64) >= 6 * sms) return launch_cfg<64, 64, 16, 4, 4, true>(g, e, s);
+        if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 2, 2, true>(g, e, s);
+        return launch_cfg<16, 16, 16, 1, 1, true>(g, e, s);
+    }
+    if (tiles_of(g, 64, 64) >= 6 * sms) return launch_cfg<64, 64, 16, 4, 4, false>(g, e, s);
+    if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 2, 2, false>(g, e, s);
+    return launch_cfg<16, 16, 16, 1, 1, false>(g, e, s);
 }
 
 Gemm mode_gemm(int d, const int64_t* n, int mu, const double* M, const double* V) {

@@ -42,55 +42,84 @@ namespace mm {
 
 namespace {
 
+// Position of natural-order element i in the mode-1 layout (fibres of n at pitch
+// p): 32-bit division when the tensor allows it.
+__device__ __forceinline__ int64_t mode1_pos(int64_t i, int n, int p, int64_t N) {
+    if (N < (int64_t(1) << 31)) {
+        const uint32_t q = (uint32_t)i / (uint32_t)n;
+        return ((uint32_t)i - q * (uint32_t)n) + (int64_t)p * q;
+    }
+    return (i % n) + (int64_t)p * (i / n);
+}
+
 __device__ __forceinline__ void flag_nonfinite_bits(const Epi& e, double v) {
     if (!mx::finite_bits(v) && e.status) atomicOr(e.status, MM_STATUS_NONFINITE);
 }
 
-// The integrator epilogue of the mixed forms.
+// The integrator epilogue of the mixed forms, element i.
+__device__ __forceinline__ void update_one(const Epi& e, int64_t i, float yi, double ui, int64_t N, float alphaf,
+                                           float t0f, float t1f) {
+    switch (e.kind) {
+    case EPI_STORE:
+        e.C[i] = e.alpha * mx::f2d(yi);
+        break;
+    case EPI_EE: {
+        const double v = fma(e.alpha, mx::f2d(yi), ui);
+        flag_nonfinite_bits(e, v);
+        e.U[i] = v;
+        break;
+    }
+    case EPI_ETD_S1: {
+        e.U2[i] = fma(e.alpha, mx::f2d(yi), ui);
+        float uh, ul;
+        mx::d2ff(ui, uh, ul);
+        const float w2 = mx::dg32(e.g, uh + ul, alphaf * yi, t0f, t1f, i);
+        store_parts_prec(e.prec, e.W2p, e.w2_pitch, mode1_pos(i, e.w2_n, e.w2_p, N), w2, 0.f);
+        break;
+    }
+    case EPI_ETD_S1_NOG:
+        e.U2[i] = fma(e.alpha, mx::f2d(yi), ui);
+        break;
+    case EPI_ETD_S2: {
+        const double v = fma(e.alpha, mx::f2d(yi), ui);
+        flag_nonfinite_bits(e, v);
+        e.U[i] = v;
+        break;
+    }
+    case EPI_LAWSON2: {
+        float uh, ul;
+        mx::d2ff(ui, uh, ul);
+        const float gv = (float)e.beta * mx::g32(e.g, uh + ul, t1f, i);
+        const double v = fma(e.alpha, mx::f2d(yi), mx::f2d(gv));
+        flag_nonfinite_bits(e, v);
+        e.U[i] = v;
+        break;
+    }
+    default: break;
+    }
+}
+
+// Four elements per thread and pass, their loads issued together (the pass is
+// bound by memory latency otherwise); the state read is U (exp. Euler, ETD2RK
+// stage 1) or U2 (stage 2, Lawson2b).
 __global__ void __launch_bounds__(256) mixed_update_kernel(const float* __restrict__ y, Epi e,
                                                            int64_t N, float alphaf, float t0f, float t1f) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float yi = __ldg(y + i);
-        switch (e.kind) {
-        case EPI_STORE:
-            e.C[i] = e.alpha * mx::f2d(yi);
-            break;
-        case EPI_EE: {
-            const double v = fma(e.alpha, mx::f2d(yi), e.U[i]);
-            flag_nonfinite_bits(e, v);
-            e.U[i] = v;
-            break;
+    const double* src = (e.kind == EPI_ETD_S2 || e.kind == EPI_LAWSON2) ? e.U2 : e.U;
+    const bool reads = e.kind != EPI_STORE;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+        float yv[4];
+        double uv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * stride;
+            yv[k] = i < N ? __ldg(y + i) : 0.f;
+            uv[k] = (reads && i < N) ? __ldg(src + i) : 0.0;
         }
-        case EPI_ETD_S1: {
-            const double u = e.U[i];
-            e.U2[i] = fma(e.alpha, mx::f2d(yi), u);
-            float uh, ul;
-            mx::d2ff(u, uh, ul);
-            const float w2 = mx::dg32(e.g, uh + ul, alphaf * yi, t0f, t1f, i);
-            const int64_t pos = (i % e.w2_n) + (int64_t)e.w2_p * (i / e.w2_n);
-            store_parts_prec(e.prec, e.W2p, e.w2_pitch, pos, w2, 0.f);
-            break;
-        }
-        case EPI_ETD_S1_NOG:
-            e.U2[i] = fma(e.alpha, mx::f2d(yi), e.U[i]);
-            break;
-        case EPI_ETD_S2: {
-            const double v = fma(e.alpha, mx::f2d(yi), e.U2[i]);
-            flag_nonfinite_bits(e, v);
-            e.U[i] = v;
-            break;
-        }
-        case EPI_LAWSON2: {
-            float uh, ul;
-            mx::d2ff(e.U2[i], uh, ul);
-            const float gv = (float)e.beta * mx::g32(e.g, uh + ul, t1f, i);
-            const double v = fma(e.alpha, mx::f2d(yi), mx::f2d(gv));
-            flag_nonfinite_bits(e, v);
-            e.U[i] = v;
-            break;
-        }
-        default: break;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t i = i0 + k * stride;
+            if (i < N) update_one(e, i, yv[k], uv[k], N, alphaf, t0f, t1f);
         }
     }
 }
@@ -101,7 +130,7 @@ __global__ void __launch_bounds__(256) split_input_kernel(const double* __restri
          i += (int64_t)gridDim.x * blockDim.x) {
         float h, l;
         mx::d2ff(__ldg(V + i), h, l);
-        store_parts_prec(prec, parts, pitch, (i % n1) + (int64_t)p1 * (i / n1), h, l);
+        store_parts_prec(prec, parts, pitch, mode1_pos(i, n1, p1, N), h, l);
     }
 }
 
@@ -111,7 +140,7 @@ __global__ void __launch_bounds__(256) diff_split_kernel(const float* __restrict
                                                          int64_t N) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x)
-        store_parts_prec(prec, parts, pitch, (i % n1) + (int64_t)p1 * (i / n1), __ldg(ya + i) - __ldg(yb + i), 0.f);
+        store_parts_prec(prec, parts, pitch, mode1_pos(i, n1, p1, N), __ldg(ya + i) - __ldg(yb + i), 0.f);
 }
 
 int64_t grid_of(int64_t N) { return std::min<int64_t>((N + 255) / 256, (int64_t)num_sms() * 16); }

@@ -8,9 +8,13 @@
 // The paper evaluates the scaled functions by Gauss-Lobatto quadrature of
 // eq. (4a); here the scaled phi_L (L = ell_max) is the truncated Taylor series
 // of eq. (4b) in Horner form, and phi_{l-1}(Y) = Y phi_l(Y) + I/(l-1)! gives
-// the lower ones.  With ||Y||_1 <= 1/2 and 16 Taylor terms the truncation is
-// below 2^-17/17! ~ 2e-20 relative to ||phi_L||, so every phi_l(Y) is exact
-// to rounding; all products run through the FP64 contraction kernel.
+// the lower ones.  With ||Y||_1 <= 1 and 18 Taylor terms the truncation is below
+// 1/19! ~ 8e-18 relative to ||phi_L||, so every phi_l(Y) is exact to rounding
+// (the terms Y^i/(i+L)! never exceed 1/L!, so the alternating sum of a
+// dissipative Y cancels little).  Scaling to 1 rather than lower keeps the
+// number of squarings, whose rounding the later squarings amplify, to the
+// minimum; all products run through the FP64 contraction kernel with two-level
+// summation.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -23,7 +27,7 @@ namespace mm {
 
 namespace {
 
-constexpr int kTaylorTerms = 16;
+constexpr int kTaylorTerms = 18;
 
 __global__ void scale_copy_kernel(const double* __restrict__ src, double* __restrict__ dst,
                                   double a, int64_t count) {
@@ -97,6 +101,7 @@ int square_gemm(int n, const double* A, const double* B, double* C, double alpha
     g.A = A; g.lda = n;
     g.B = B; g.ldb = n; g.b_kcontig = 1;
     g.ldc = n;
+    g.two_level = 1;
     Epi e{};
     e.kind = EPI_STORE;
     e.alpha = alpha; e.beta = beta; e.gamma = gamma; e.delta = delta; e.diag = diag;
@@ -139,7 +144,7 @@ int form_phis(int n, const double* A, double tau, int L, double* const* out, dou
     if (!isfinite(norm1)) { rc = MM_ERR_ARG; goto done; }
     {
         int sq = 0;
-        while (sq < 1000 && ldexp(norm1, -sq) > 0.5) ++sq;
+        while (sq < 1000 && ldexp(norm1, -sq) > 1.0) ++sq;
         *s_out = sq;
         *band_out = band;
         // Y = tau A / 2^s

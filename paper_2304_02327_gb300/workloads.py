@@ -228,6 +228,9 @@ def workload(name: str, **over) -> Problem:
         "ac2d_n64_expeuler": lambda: allen_cahn_2d(64, 0.01, 1, 1e-3, 50, EXPEULER),
         "adr3d_n128_etd2rk": lambda: adr_3d(128, 0.5, 1.0, 2, 1e-3, 100, ETD2RK),
         "adr3d_n320_etd2rk": lambda: adr_3d(320, 0.5, 1.0, 3, 1e-3, 100, ETD2RK),
+        # the same problem at n = 256 (N = 16.8M, operands still larger than L2): the
+        # size on which kernel profiles are captured
+        "adr3d_n256_etd2rk": lambda: adr_3d(256, 0.5, 1.0, 3, 1e-3, 100, ETD2RK),
         "riccati_n2048_expeuler": lambda: riccati_2d(2048, 5, 1e-4, 50, EXPEULER),
         "riccati_n2048_etd2rk": lambda: riccati_2d(2048, 5, 1e-4, 50, ETD2RK),
     }
