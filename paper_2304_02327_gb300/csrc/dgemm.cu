@@ -155,13 +155,15 @@ int launch_dgemm(const Gemm& g, const Epi& e, cudaStream_t s) {
     const int64_t sms = num_sms();
     // Largest tile whose grid still fills the machine several times; smaller
     // tiles trade operand reuse (irrelevant when DFMA-bound) for balance.
+    // 32 x 32 tiles use 64 threads of 4 x 4 outputs: two FMAs per shared-memory
+    // load (2 x 2 outputs would give one, and the shared-memory pipe would bind).
     if (g.two_level) {
         if (tiles_of(g, 64, 64) >= 6 * sms) return launch_cfg<64, 64, 16, 4, 4, true>(g, e, s);
-        if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 2, 2, true>(g, e, s);
+        if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 4, 4, true>(g, e, s);
         return launch_cfg<16, 16, 16, 1, 1, true>(g, e, s);
     }
     if (tiles_of(g, 64, 64) >= 6 * sms) return launch_cfg<64, 64, 16, 4, 4, false>(g, e, s);
-    if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 2, 2, false>(g, e, s);
+    if (tiles_of(g, 32, 32) >= 3 * sms) return launch_cfg<32, 32, 16, 4, 4, false>(g, e, s);
     return launch_cfg<16, 16, 16, 1, 1, false>(g, e, s);
 }
 
