@@ -239,9 +239,9 @@ MM_API int tucker_apply_noalloc(int d, const int64_t* n, const double* const* M,
  * K u + g prepass, one persistent tensor-core launch per direction over the tiles
  * of every instance, the FP64 update), captured once in a CUDA graph.
  *
- * mm_tune: autotune = 1 times the candidate tile widths nc in {128, 96, 64} on the
- * batch's own Tucker launches at creation and keeps the fastest; nc_cap = 16..128
- * (a multiple of 16) fixes the width instead (0: autotune or 128); graph = 1 makes
+ * mm_tune: autotune = 1 times the candidate tile widths nc in {160, 128, 96, 64} on
+ * the batch's own Tucker launches at creation and keeps the fastest; nc_cap = 16..160
+ * (a multiple of 16) fixes the width instead (0: autotune or 160); graph = 1 makes
  * expint_batch_run replay a captured graph of its nsteps steps (0: plain launches).
  * A NULL mm_tune means {autotune 0, nc_cap 0, graph 1}. */
 typedef struct mm_tune {

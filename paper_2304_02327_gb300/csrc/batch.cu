@@ -31,7 +31,7 @@ namespace mm {
 namespace {
 
 constexpr int kChunk = 8192;           // elements per chunk of the elementwise passes
-constexpr int kNcCandidates[] = {128, 96, 64};
+constexpr int kNcCandidates[] = {160, 128, 96, 64};
 
 struct BInst {                         // device table, one entry per instance
     double* U;
@@ -54,7 +54,7 @@ struct BInst {                         // device table, one entry per instance
 // contiguous range, so it locates its instance once and then walks forward.
 constexpr int kT = 32;
 
-__global__ void __launch_bounds__(256) batch_prepass_kernel(const BInst* __restrict__ tab,
+__global__ void __launch_bounds__(256, 6) batch_prepass_kernel(const BInst* __restrict__ tab,
                                                             const int64_t* __restrict__ tile_begin, int count,
                                                             int64_t ntiles, float t, int prec) {
     __shared__ float2 sp[kT + 2][kT + 2];
@@ -292,7 +292,7 @@ std::vector<std::pair<int, int>> size_classes(int count, const int64_t* n1, cons
 extern "C" int mm_batch_tile_plan(int count, const int64_t* n1, const int64_t* n2, int prec, int nc_cap,
                                   int mode, int32_t* tiles, int64_t max_tiles, int64_t* ntiles) {
     if (count < 1 || !n1 || !n2 || !ntiles || (mode != 1 && mode != 2)) return MM_ERR_ARG;
-    if ((prec != MM_TF32X3 && prec != MM_BF16X3) || nc_cap < 16 || nc_cap > 128 || nc_cap % 16) return MM_ERR_ARG;
+    if ((prec != MM_TF32X3 && prec != MM_BF16X3) || nc_cap < 16 || nc_cap > 160 || nc_cap % 16) return MM_ERR_ARG;
     for (int j = 0; j < count; ++j)
         if (n1[j] < 1 || n1[j] > 8192 || n2[j] < 1 || n2[j] > 8192) return MM_ERR_SHAPE;
     std::vector<int> cls_of;
@@ -358,9 +358,9 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
     b->cls.resize(sizes.size());
     b->spec1.resize(sizes.size());
     b->spec2.resize(sizes.size());
-    b->nc_cap.assign(sizes.size(), 128);
+    b->nc_cap.assign(sizes.size(), 160);
     if (tune && tune->nc_cap) {
-        if (tune->nc_cap < 16 || tune->nc_cap > 128 || tune->nc_cap % 16) { delete b; return MM_ERR_ARG; }
+        if (tune->nc_cap < 16 || tune->nc_cap > 160 || tune->nc_cap % 16) { delete b; return MM_ERR_ARG; }
         for (auto& v : b->nc_cap) v = tune->nc_cap;
     }
     for (int j = 0; j < count; ++j) b->cls[cls_of[j]].members.push_back(j);

@@ -15,6 +15,7 @@
 
 namespace mm {
 
+// kBK: values of one pipeline stage along K (one 128-byte swizzle row: four MMAs).
 struct FormTF32 {
     static constexpr int kElem = 4, kBK = 32, kAParts = 2;
     static constexpr int kCorr = 3;   // a1 b0, a0 b1, a0 b2

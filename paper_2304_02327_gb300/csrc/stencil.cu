@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(256) split_pairs_kernel(const double* __restri
 
 // One thread per element (flat index, i_1 fastest); the neighbours' pairs come
 // from L1/L2, differences are taken pairwise so they keep their own accuracy.
-__global__ void __launch_bounds__(256) prepass_mixed_kernel(StencilArgsMixed a) {
+__global__ void __launch_bounds__(256, 6) prepass_mixed_kernel(StencilArgsMixed a) {
     for (int64_t off = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; off < a.N;
          off += (int64_t)gridDim.x * blockDim.x) {
         float uh, ul;

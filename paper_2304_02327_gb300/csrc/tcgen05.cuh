@@ -166,6 +166,19 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t addr) {
     return d;
 }
 
+// The same for the 64-byte swizzle: rows of 64 bytes, 8-row atoms of 512 bytes
+// (SBO), the tile base 512-byte aligned; `addr` may carry an in-row K offset
+// (0 or 32 B, one MMA's K slice).
+__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
+    d |= (uint64_t)(512 >> 4) << 32;                   // stride byte offset: 8-row atom
+    d |= (uint64_t)1 << 46;                            // descriptor version (sm_100 family)
+    d |= (uint64_t)4 << 61;                            // swizzle: 64 B
+    return d;
+}
+
 // Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4)                       // D format f32

@@ -59,16 +59,19 @@ namespace mm {
 namespace {
 
 constexpr int kRows = 128;                 // MMA M / rows per tile
-constexpr uint32_t kATile = kRows * 128;   // bytes of one operand part tile (128-byte rows)
+constexpr uint32_t kRowBytes = 128;        // one stage's K slice of a row (128-byte swizzle)
+constexpr uint32_t kATile = kRows * kRowBytes;   // bytes of one operand part tile
 constexpr int kMaxStages = 4;
+constexpr int kGroup = 2;                  // stages whose main products share a TMEM slot
 constexpr int kBParts = 3;                 // Phi = b0 + b1 + b2 in both forms
-constexpr int kNcMax = 128;                // two sets of [main | corr] fit 512 TMEM columns
+constexpr int kNcMax = 160;                // [main slot 0 | main slot 1 | corr] fit 512 TMEM columns
 constexpr int kBars = 2 * kMaxStages + 9;  // full, empty per stage; main full/empty (slot);
                                            // corr full/empty (tile parity); mma_done
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kQuartCols = kNcMax / 4;     // columns per epilogue thread (upper bound)
+constexpr int kChunks = 3;                 // 16-column chunks per epilogue warp (4 x 3 x 16 >= kNcMax)
+constexpr int kQuartCols = 16 * kChunks;   // columns per epilogue thread (upper bound)
 constexpr int kMaxClasses = MM_TC_MAX_CLASSES;
 
 template <class F> __device__ __forceinline__ uint32_t idesc_of(int nc);
@@ -81,14 +84,6 @@ template <> __device__ __forceinline__ void mma<FormTF32>(uint32_t d, uint64_t a
 }
 template <> __device__ __forceinline__ void mma<FormBF16>(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
     tc::mma_bf16(d, a, b, id, acc);
-}
-
-// Byte offset of element k of `row` in a K-major 128-byte-swizzled tile.
-template <class F>
-__host__ __device__ __forceinline__ uint32_t sw_off(uint32_t row, uint32_t k) {
-    constexpr uint32_t per = 16 / F::kElem;     // elements per 16-byte chunk
-    return (row >> 3) * 1024u + (row & 7u) * 128u + ((((k / per) ^ (row & 7u)) & 7u) << 4) +
-           (k % per) * F::kElem;
 }
 
 // One class of tiles: instances of equal shape whose operands sit packed one after
@@ -150,7 +145,7 @@ template <class F, int C>
 __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcGroup<C> g) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const uint32_t b_slot = (uint32_t)g.stage_nc * 128u;      // one part of the matrix tile
+    const uint32_t b_slot = (uint32_t)g.stage_nc * kRowBytes;  // one part of the matrix tile
     const uint32_t a_bytes = F::kAParts * kATile;
     const uint32_t stage_bytes = a_bytes + kBParts * b_slot;
     uint64_t* bars = (uint64_t*)(smem + g.stages * stage_bytes);
@@ -205,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                 const TcClass& k = g.cls[id.c];
                 const int row0 = id.inst * k.rows + id.rt * kRows;
                 const int col0 = id.inst * k.ncols + id.sp * k.nc;
-                const uint32_t b_tile = (uint32_t)k.nc * 128u;
+                const uint32_t b_tile = (uint32_t)k.nc * kRowBytes;
                 for (int kb = 0; kb < k.nkb; ++kb, ++it) {
                     const int s = (int)(it % stages);
                     if (it >= stages && !tc::mbar_wait(empty(s), (uint32_t)((it / stages) - 1) & 1, g.status)) {
@@ -229,43 +224,61 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            int64_t it = 0;
+            int64_t it = 0;                // stages issued
+            int64_t git = 0;               // main-slot groups issued
             int64_t uses[2] = {0, 0};      // uses of each main slot so far
             bool ok = true;
+            const uint32_t corr = tmem + (uint32_t)(2 * g.stage_nc);   // the tile's corrections
             for (int64_t i = 0; i < my_tiles && ok; ++i) {
                 const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
                 const TcClass& k = g.cls[id.c];
                 const uint32_t idd = idesc_of<F>(k.nc);
-                const int b = (int)(i & 1);
-                if (i >= 2 && !tc::mbar_wait(cempty(b), (uint32_t)((i >> 1) - 1) & 1, g.status)) break;
-                const uint32_t corr = tmem + (uint32_t)((2 + b) * g.stage_nc);
+                // main products: one TMEM slot per group of kGroup stages (a fresh slot
+                // per group, drained by the epilogue); corrections: one accumulator per
+                // tile, free again once the epilogue has read the previous tile's (its
+                // wait comes after the first stage's main products are queued)
+                int r = 0;
                 for (int kb = 0; kb < k.nkb; ++kb, ++it) {
                     const int s = (int)(it % stages);
-                    const int r = (int)(it & 1);
-                    if (uses[r] >= 1 && !tc::mbar_wait(mempty(r), (uint32_t)(uses[r] - 1) & 1, g.status)) {
-                        ok = false;
-                        break;
+                    const bool gfirst = (kb % kGroup) == 0;
+                    const bool glast = (kb % kGroup) == kGroup - 1 || kb == k.nkb - 1;
+                    if (gfirst) {
+                        r = (int)(git & 1);
+                        if (uses[r] >= 1 && !tc::mbar_wait(mempty(r), (uint32_t)(uses[r] - 1) & 1, g.status)) {
+                            ok = false;
+                            break;
+                        }
+                        ++uses[r];
                     }
-                    ++uses[r];
                     if (!tc::mbar_wait(full(s), (uint32_t)(it / stages) & 1, g.status)) { ok = false; break; }
                     tc::tc_fence_after();
                     const uint32_t mainacc = tmem + (uint32_t)(r * g.stage_nc);
                     const uint32_t abase = tc::smem_u32(smem + s * stage_bytes);
-                    const uint32_t bbase = abase + a_bytes;
-#pragma unroll 1
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t ko = kk * 32;
-                        mma<F>(mainacc, tc::desc_k_sw128(abase + ko), tc::desc_k_sw128(bbase + ko), idd, kk != 0);
+                    // descriptors of the stage's tiles; an offset of o bytes adds o / 16
+                    const uint64_t da = tc::desc_k_sw128(abase);
+                    const uint64_t db = tc::desc_k_sw128(abase + a_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma<F>(mainacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idd,
+                               (kk != 0 || !gfirst) ? 1u : 0u);
+                    if (kb == 0 && i >= 1 && !tc::mbar_wait(cempty(0), (uint32_t)((i - 1) & 1), g.status)) {
+                        ok = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
                         for (int c = 0; c < F::kCorr; ++c)
-                            mma<F>(corr, tc::desc_k_sw128(abase + F::corr_a(c) * kATile + ko),
-                                   tc::desc_k_sw128(bbase + F::corr_b(c) * b_slot + ko), idd,
+                            mma<F>(corr, da + (uint64_t)((F::corr_a(c) * kATile + kk * 32) >> 4),
+                                   db + (uint64_t)((F::corr_b(c) * b_slot + kk * 32) >> 4), idd,
                                    (c == 0 && (kb | kk) == 0) ? 0u : 1u);
-                    }
                     tc::mma_commit(empty(s));
-                    tc::mma_commit(mfull(r));
+                    if (glast) {
+                        tc::mma_commit(mfull(r));
+                        ++git;
+                    }
                 }
-                if (ok) tc::mma_commit(cfull(b));
+                if (ok) tc::mma_commit(cfull(0));
             }
             // every issued MMA has completed before TMEM can be released
             tc::mma_commit(mma_done);
@@ -277,19 +290,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
         const int cq = (warp - 2) >> 2;
         const int r = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        int64_t it = 0;
+        int64_t it = 0;                    // main-slot groups drained
         for (int64_t i = 0; i < my_tiles; ++i) {
             const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
             const TcClass& k = g.cls[id.c];
             const int nch = k.nc / 16;                        // <= 8 chunks of 16 columns
-            const int c0 = 2 * cq, c1 = min(nch, 2 * cq + 2);
-            const int b = (int)(i & 1);
+            const int c0 = kChunks * cq, c1 = min(nch, kChunks * cq + kChunks);
             float acc[kQuartCols];
 #pragma unroll
             for (int u = 0; u < kQuartCols; ++u) acc[u] = 0.f;
             bool ok = true;
-            // main product, one K-block slot at a time, summed in FP32 registers
-            for (int kb = 0; kb < k.nkb && ok; ++kb, ++it) {
+            // main product, one slot (kGroup stages) at a time, summed in FP32 registers
+            const int ngroups = (k.nkb + kGroup - 1) / kGroup;
+            for (int gi = 0; gi < ngroups && ok; ++gi, ++it) {
                 const int rs = (int)(it & 1);
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(mfull(rs), (uint32_t)(it >> 1) & 1, g.status));
                 if (!ok) break;
@@ -310,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                 if (lane == 0) tc::mbar_arrive(mempty(rs));
             }
             if (!ok) break;
-            ok = __all_sync(0xffffffffu, tc::mbar_wait(cfull(b), (uint32_t)(i >> 1) & 1, g.status));
+            ok = __all_sync(0xffffffffu, tc::mbar_wait(cfull(0), (uint32_t)(i & 1), g.status));
             if (!ok) break;
             tc::tc_fence_after();
             const int64_t q = (int64_t)id.rt * kRows + r;
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             // next-mode layout of output (q, i): position jq + p' (rq + (R / n') i)
             int64_t jq = 0, rq = 0;
             if (!k.last) { jq = q % k.next_n; rq = q / k.next_n; }
-            const uint32_t cset = tmem + lane_off + (uint32_t)((2 + b) * g.stage_nc);
+            const uint32_t cset = tmem + lane_off + (uint32_t)(2 * g.stage_nc);
 #pragma unroll
             for (int c = 0; c < kQuartCols / 16; ++c) {    // y = corrections + main, in FP32
                 if (c0 + c < c1) {
@@ -332,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             }
             tc::tc_fence_before();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(cempty(b));      // corrections read: TMEM set free
+            if (lane == 0) tc::mbar_arrive(cempty(0));      // corrections read: accumulator free
             if (!valid) continue;
             // output column col of row q: next-mode position jq + p' (rq + (R / n') col)
             // (or q + ldy col for FP32); successive columns step by dpos
@@ -413,8 +426,8 @@ struct Geometry {
     int nc, splits;
 };
 
-// Columns per CTA tile given at most nc_cap (a multiple of 16, <= 128): the fewest
-// splits, then the narrowest multiple of 16 that covers the columns.
+// Columns per CTA tile given at most nc_cap (a multiple of 16, <= kNcMax): the
+// fewest splits, then the narrowest multiple of 16 that covers the columns.
 Geometry split_cols(int ncols, int nc_cap) {
     const int n16 = round_up(ncols, 16);
     Geometry g;
@@ -424,9 +437,13 @@ Geometry split_cols(int ncols, int nc_cap) {
     return g;
 }
 
-// One product alone on the GPU: among the column splittings, take the one whose
-// tile waves over the SMs cost least, a tile costing its columns plus a fixed
-// 32-column-equivalent overhead (the operand tile re-read, the epilogue's fixed work).
+// Relative time of one tile of width nc: a tcgen05.mma of M = 128 takes the same
+// time for every N up to 160 (measured), so a tile costs about the same whatever
+// its width, plus an epilogue share that grows with nc.
+int64_t tile_cost(int nkb, int nc) { return (int64_t)nkb * (256 + nc); }
+
+// One product alone on the GPU: among the column splittings, the one whose tile
+// waves over the SMs cost least.
 Geometry geometry_single(int ncols, int64_t rows) {
     const int n16 = round_up(ncols, 16);
     const int64_t row_tiles = (rows + kRows - 1) / kRows;
@@ -437,7 +454,7 @@ Geometry geometry_single(int ncols, int64_t rows) {
     for (int sp = s_min; sp <= 2 * s_min && sp <= n16 / 16; ++sp) {
         const Geometry g = split_cols(ncols, round_up((n16 + sp - 1) / sp, 16));
         const int64_t waves = (row_tiles * g.splits + sms - 1) / sms;
-        const int64_t cost = waves * (g.nc + 32);
+        const int64_t cost = waves * tile_cost(1, g.nc);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
             best = g;
@@ -449,7 +466,7 @@ Geometry geometry_single(int ncols, int64_t rows) {
 // Pipeline depth and dynamic shared memory for tiles up to stage_nc columns.
 template <class F>
 int stages_for(int stage_nc, int* stages, size_t* smem) {
-    const size_t stage = (size_t)F::kAParts * kATile + kBParts * (size_t)stage_nc * 128;
+    const size_t stage = (size_t)F::kAParts * kATile + kBParts * (size_t)stage_nc * kRowBytes;
     const size_t fixed = 1024 + kBars * 8 + 16;
     int st = (int)((kSmemLimit - fixed) / stage);
     st = std::min(st, kMaxStages);
@@ -638,7 +655,7 @@ int tc_group_tiles(int prec, const TcClassSpec* cls, int ncls, const int* nc_cap
         const Geometry geo = split_cols(cls[c].ncols, nc_cap[c]);
         const int nkb = (cls[c].X.n + bk - 1) / bk;
         const int rt = (cls[c].rows + kRows - 1) / kRows;
-        const int64_t cost = (int64_t)nkb * (geo.nc + 32);
+        const int64_t cost = tile_cost(nkb, geo.nc);
         for (int j = 0; j < cls[c].count; ++j)
             for (int r = 0; r < rt; ++r)
                 for (int sp = 0; sp < geo.splits; ++sp) v.push_back({cost, make_int4(c, j, r, sp)});

@@ -245,6 +245,9 @@ def workload(name: str, **over) -> Problem:
 # Batches of independent problems, named by what they are.
 BATCHED = {
     "batch_ac2d_1024_expeuler": lambda: batched_allen_cahn(1024, 4, 1e-3, 20),
+    # the first 256 instances of the same draw: the size on which kernel profiles are
+    # captured (about 2 GB on the device with the comparison loop's plans)
+    "batch_ac2d_256_expeuler": lambda: batched_allen_cahn(1024, 4, 1e-3, 20)[:256],
 }
 
 

@@ -67,7 +67,7 @@ def test_batch_matches_oracle_per_instance(api, form):
         assert rel_err_inf(g, ref) <= TOL_STEP and rel_err_fro(g, ref) <= TOL_STEP, p.name
 
 
-@pytest.mark.parametrize("nc_cap", [128, 64, 48])
+@pytest.mark.parametrize("nc_cap", [160, 128, 64, 48])
 def test_batch_equals_single_problem_path_bitwise(api, form, nc_cap):
     probs = small_batch(steps=5)
     got, _ = run_batch(api, probs, form, 5, autotune=False, nc_cap=nc_cap)
@@ -95,7 +95,7 @@ def test_batch_graph_and_plain_launches_agree(api, form):
 def test_batch_autotune_picks_a_candidate(api, form):
     probs = small_batch(steps=2)
     _, b = run_batch(api, probs, form, 2, autotune=True)
-    assert b.info()["nc_cap"] in (128, 96, 64)
+    assert b.info()["nc_cap"] in (160, 128, 96, 64)
 
 
 def test_batch_rejects_unsupported(api):
