@@ -53,8 +53,22 @@ struct BInst {                         // device table, one entry per instance
 // (tile_begin holds each instance's first tile) and each block takes one
 // contiguous range, so it locates its instance once and then walks forward.
 constexpr int kT = 32;
+constexpr int kHalo = (kT + 2) * (kT + 2);          // 1156 values of a tile with its halo
+constexpr int kPer = (kHalo + 255) / 256;           // of them per thread
 
-__global__ void __launch_bounds__(256, 6) batch_prepass_kernel(const BInst* __restrict__ tab,
+struct TileAt {
+    int inst, a1, a2;
+};
+
+__device__ __forceinline__ TileAt tile_at(const BInst* __restrict__ tab, const int64_t* __restrict__ tile_begin,
+                                          int inst, int64_t T) {
+    const int n1 = tab[inst].n1;
+    const int tiles1 = (n1 + kT - 1) / kT;
+    const int lt = (int)(T - __ldg(tile_begin + inst));
+    return TileAt{inst, (lt % tiles1) * kT, (lt / tiles1) * kT};
+}
+
+__global__ void __launch_bounds__(256) batch_prepass_kernel(const BInst* __restrict__ tab,
                                                             const int64_t* __restrict__ tile_begin, int count,
                                                             int64_t ntiles, float t, int prec) {
     __shared__ float2 sp[kT + 2][kT + 2];
@@ -68,22 +82,41 @@ __global__ void __launch_bounds__(256, 6) batch_prepass_kernel(const BInst* __re
         else hi = mid;
     }
     int64_t next = __ldg(tile_begin + inst + 1);
-    for (int64_t T = T0; T < T1; ++T) {
-        while (T >= next) next = __ldg(tile_begin + (++inst) + 1);
-        const BInst b = tab[inst];      // by value: the stores below cannot alias it
-        const double* U = b.U;
-        const int n1 = b.n1, n2 = b.n2;
-        const int tiles1 = (n1 + kT - 1) / kT;
-        const int lt = (int)(T - __ldg(tile_begin + inst));
-        const int a1 = (lt % tiles1) * kT, a2 = (lt / tiles1) * kT;
-        for (int e = threadIdx.x; e < (kT + 2) * (kT + 2); e += blockDim.x) {
+    double raw[kPer];
+    // global loads of a tile's halo region, left in flight
+    auto fetch = [&](const TileAt& ta) {
+        const double* U = tab[ta.inst].U;
+        const int n1 = tab[ta.inst].n1, n2 = tab[ta.inst].n2;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int e = threadIdx.x + 256 * k;
             const int r = e / (kT + 2), c = e % (kT + 2);
-            const int i1 = a1 - 1 + c, i2 = a2 - 1 + r;
-            float2 v = make_float2(0.f, 0.f);
-            if (i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2) mx::d2ff(__ldg(U + i1 + (int64_t)n1 * i2), v.x, v.y);
-            sp[r][c] = v;
+            const int i1 = ta.a1 - 1 + c, i2 = ta.a2 - 1 + r;
+            raw[k] = (e < kHalo && i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2) ? __ldg(U + i1 + (int64_t)n1 * i2)
+                                                                             : 0.0;
+        }
+    };
+    TileAt cur = tile_at(tab, tile_begin, inst, T0);
+    fetch(cur);
+    for (int64_t T = T0; T < T1; ++T) {
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const int e = threadIdx.x + 256 * k;
+            if (e < kHalo) {
+                float2 v;
+                mx::d2ff(raw[k], v.x, v.y);
+                (&sp[0][0])[e] = v;
+            }
+        }
+        const BInst b = tab[cur.inst];  // by value: the stores below cannot alias it
+        const int a1 = cur.a1, a2 = cur.a2;
+        if (T + 1 < T1) {                // the next tile's loads overlap this tile's stencil
+            while (T + 1 >= next) next = __ldg(tile_begin + (++inst) + 1);
+            cur = tile_at(tab, tile_begin, inst, T + 1);
+            fetch(cur);
         }
         __syncthreads();
+        const int n1 = b.n1, n2 = b.n2;
         const int c = threadIdx.x % kT;
         const int i1 = a1 + c;
 #pragma unroll

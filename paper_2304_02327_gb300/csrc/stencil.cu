@@ -120,6 +120,173 @@ __global__ void __launch_bounds__(256, 6) prepass_mixed_kernel(StencilArgsMixed 
     }
 }
 
+// K u + g of the mixed prepass for d = 2 and d = 3 in one pass: the state is read
+// once and split once into (hi, lo) pairs held in shared memory, the stencil reads
+// its neighbours there (same operations, in the same order, as
+// prepass_mixed_kernel).  d = 2: one 32 x 32 tile and its halo per step of the
+// block loop.  d = 3: a 32 x 16 tile of (i_1, i_2) marches along i_3 through a
+// ring of three planes, so every plane is split once per tile.
+constexpr int kT1 = 32;
+
+__device__ __forceinline__ float stencil_extras(const StencilArgsMixed& a, float acc, int64_t off) {
+    if (a.yadd) acc += __ldg(a.yadd + off);
+    if (a.yadd2) acc += __ldg(a.yadd2 + off);
+    if (a.cadd) {
+        float ch, cl;
+        mx::d2ff(__ldg(a.cadd + off), ch, cl);
+        acc += ch + cl;
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float stencil_dir(const float* __restrict__ cf, int nm, int i, float u, float uh, float ul,
+                                             float2 lo_nb, float2 hi_nb, float acc) {
+    acc = fmaf(__ldg(cf + 2 * nm + i), u, acc);
+    if (i > 0) acc = fmaf(__ldg(cf + i), (lo_nb.x - uh) + (lo_nb.y - ul), acc);
+    if (i + 1 < nm) acc = fmaf(__ldg(cf + nm + i), (hi_nb.x - uh) + (hi_nb.y - ul), acc);
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) stencil2d_kernel(StencilArgsMixed a) {
+    __shared__ float2 sp[kT1 + 2][kT1 + 2];
+    const int n1 = (int)a.n[0], n2 = (int)a.n[1];
+    const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT1 - 1) / kT1;
+    for (int T = blockIdx.x; T < t1 * t2; T += gridDim.x) {
+        const int a1 = (T % t1) * kT1, a2 = (T / t1) * kT1;
+        for (int e = threadIdx.x; e < (kT1 + 2) * (kT1 + 2); e += blockDim.x) {
+            const int r = e / (kT1 + 2), c = e % (kT1 + 2);
+            const int i1 = a1 - 1 + c, i2 = a2 - 1 + r;
+            float2 v = make_float2(0.f, 0.f);
+            if (i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2) mx::d2ff(__ldg(a.U + i1 + (int64_t)n1 * i2), v.x, v.y);
+            sp[r][c] = v;
+        }
+        __syncthreads();
+        const int c = threadIdx.x % kT1;
+        const int i1 = a1 + c;
+#pragma unroll
+        for (int q = 0; q < kT1 / 8; ++q) {
+            const int r = threadIdx.x / kT1 + 8 * q;
+            const int i2 = a2 + r;
+            if (i1 >= n1 || i2 >= n2) continue;
+            const float uh = sp[r + 1][c + 1].x, ul = sp[r + 1][c + 1].y;
+            const float u = uh + ul;
+            const int64_t off = i1 + (int64_t)n1 * i2;
+            float acc = mx::g32(a.g, u, a.t, off);
+            acc = stencil_dir(a.coef[0], n1, i1, u, uh, ul, sp[r + 1][c], sp[r + 1][c + 2], acc);
+            acc = stencil_dir(a.coef[1], n2, i2, u, uh, ul, sp[r][c + 1], sp[r + 2][c + 1], acc);
+            acc = stencil_extras(a, acc, off);
+            store_parts_prec(a.prec, a.Wp, a.part_pitch, i1 + (int64_t)a.p1 * i2, acc, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+constexpr int kT2 = 16;      // i_2 extent of a 3D tile
+constexpr int kZ = 32;       // planes per block of the 3D march
+constexpr int kHalo3 = (kT2 + 2) * (kT1 + 2);      // 612 values of a plane with its halo
+constexpr int kPer3 = (kHalo3 + 255) / 256;         // of them per thread
+
+// The coefficient of the missing neighbour at a grid edge is exactly zero and the
+// halo there holds zeros, so the edge terms add exact zeros and need no branch.
+__device__ __forceinline__ float stencil_term(float a, float2 nb, float uh, float ul, float acc) {
+    return fmaf(a, (nb.x - uh) + (nb.y - ul), acc);
+}
+
+__global__ void __launch_bounds__(256, 4) stencil3d_kernel(StencilArgsMixed a) {
+    __shared__ float2 sp[3][kT2 + 2][kT1 + 2];
+    const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = (int)a.n[2];
+    const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT2 - 1) / kT2, tz = (n3 + kZ - 1) / kZ;
+    const int64_t plane = (int64_t)n1 * n2;
+    const float* cf1 = a.coef[0];
+    const float* cf2 = a.coef[1];
+    const float* cf3 = a.coef[2];
+    const int c = threadIdx.x % kT1;
+    for (int T = blockIdx.x; T < t1 * t2 * tz; T += gridDim.x) {
+        const int a1 = (T % t1) * kT1, a2 = ((T / t1) % t2) * kT2, z0 = (T / (t1 * t2)) * kZ;
+        const int z1 = min(n3, z0 + kZ);
+        // this thread's share of a plane's halo region: offsets, validity
+        int64_t goff[kPer3];
+        bool gin[kPer3];
+#pragma unroll
+        for (int k = 0; k < kPer3; ++k) {
+            const int e = threadIdx.x + 256 * k;
+            const int r = e / (kT1 + 2), cc = e % (kT1 + 2);
+            const int i1 = a1 - 1 + cc, i2 = a2 - 1 + r;
+            gin[k] = e < kHalo3 && i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2;
+            goff[k] = gin[k] ? i1 + (int64_t)n1 * i2 : 0;
+        }
+        double raw[kPer3];
+        auto fetch = [&](int z) {           // global loads of plane z, left in flight
+#pragma unroll
+            for (int k = 0; k < kPer3; ++k)
+                raw[k] = (gin[k] && z >= 0 && z < n3) ? __ldg(a.U + goff[k] + plane * z) : 0.0;
+        };
+        auto deposit = [&](int z) {         // split them into ring slot z mod 3
+            float2* dst = &sp[(z + 3) % 3][0][0];
+#pragma unroll
+            for (int k = 0; k < kPer3; ++k) {
+                const int e = threadIdx.x + 256 * k;
+                if (e < kHalo3) {
+                    float2 v;
+                    mx::d2ff(raw[k], v.x, v.y);
+                    dst[e] = v;
+                }
+            }
+        };
+        fetch(z0 - 1);
+        deposit(z0 - 1);
+        fetch(z0);
+        deposit(z0);
+        fetch(z0 + 1);
+        // coefficients along i_1 and i_2 are fixed for this thread's outputs
+        const int i1 = a1 + c;
+        const bool in1 = i1 < n1;
+        const float a1a = in1 ? __ldg(cf1 + i1) : 0.f, a1c = in1 ? __ldg(cf1 + n1 + i1) : 0.f,
+                    a1s = in1 ? __ldg(cf1 + 2 * n1 + i1) : 0.f;
+        float a2a[kT2 / 8], a2c[kT2 / 8], a2s[kT2 / 8];
+#pragma unroll
+        for (int q = 0; q < kT2 / 8; ++q) {
+            const int i2 = a2 + threadIdx.x / kT1 + 8 * q;
+            const bool in2 = i2 < n2;
+            a2a[q] = in2 ? __ldg(cf2 + i2) : 0.f;
+            a2c[q] = in2 ? __ldg(cf2 + n2 + i2) : 0.f;
+            a2s[q] = in2 ? __ldg(cf2 + 2 * n2 + i2) : 0.f;
+        }
+        for (int z = z0; z < z1; ++z) {
+            deposit(z + 1);
+            fetch(z + 2);                   // in flight during this plane's stencil
+            __syncthreads();
+            const float2(*pm)[kT1 + 2] = sp[(z + 2) % 3];
+            const float2(*p0)[kT1 + 2] = sp[z % 3];
+            const float2(*pp)[kT1 + 2] = sp[(z + 1) % 3];
+            const float a3a = __ldg(cf3 + z), a3c = __ldg(cf3 + n3 + z), a3s = __ldg(cf3 + 2 * n3 + z);
+#pragma unroll
+            for (int q = 0; q < kT2 / 8; ++q) {
+                const int r = threadIdx.x / kT1 + 8 * q;
+                const int i2 = a2 + r;
+                if (!in1 || i2 >= n2) continue;
+                const float uh = p0[r + 1][c + 1].x, ul = p0[r + 1][c + 1].y;
+                const float u = uh + ul;
+                const int64_t off = i1 + (int64_t)n1 * i2 + plane * z;
+                float acc = mx::g32(a.g, u, a.t, off);
+                acc = fmaf(a1s, u, acc);
+                acc = stencil_term(a1a, p0[r + 1][c], uh, ul, acc);
+                acc = stencil_term(a1c, p0[r + 1][c + 2], uh, ul, acc);
+                acc = fmaf(a2s[q], u, acc);
+                acc = stencil_term(a2a[q], p0[r][c + 1], uh, ul, acc);
+                acc = stencil_term(a2c[q], p0[r + 2][c + 1], uh, ul, acc);
+                acc = fmaf(a3s, u, acc);
+                acc = stencil_term(a3a, pm[r + 1][c + 1], uh, ul, acc);
+                acc = stencil_term(a3c, pp[r + 1][c + 1], uh, ul, acc);
+                acc = stencil_extras(a, acc, off);
+                store_parts_prec(a.prec, a.Wp, a.part_pitch,
+                                 i1 + (int64_t)a.p1 * (i2 + (int64_t)n2 * z), acc, 0.f);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void stencil_coef_kernel(const double* __restrict__ A, int n, float* coef) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double a = i > 0 ? A[i + (int64_t)n * (i - 1)] : 0.0;
@@ -136,6 +303,18 @@ __global__ void stencil_coef_kernel(const double* __restrict__ A, int n, float* 
 int launch_prepass_mixed(const StencilArgsMixed& a0, float2* Up, cudaStream_t s) {
     const int64_t blocks = std::min<int64_t>((a0.N + 255) / 256, (int64_t)num_sms() * 16);
     StencilArgsMixed a = a0;
+    if (a.mode == PRE_KU_G && (a.d == 2 || a.d == 3)) {
+        const int64_t t1 = (a.n[0] + kT1 - 1) / kT1;
+        const int64_t tiles = a.d == 2 ? t1 * ((a.n[1] + kT1 - 1) / kT1)
+                                       : t1 * ((a.n[1] + kT2 - 1) / kT2) * ((a.n[2] + kZ - 1) / kZ);
+        if (tiles > 0x7fffffffLL) return MM_ERR_SHAPE;
+        const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)num_sms() * 8);
+        TraceScope tr(KC_PREPASS, s);
+        if (a.d == 2) stencil2d_kernel<<<grid, 256, 0, s>>>(a);
+        else stencil3d_kernel<<<grid, 256, 0, s>>>(a);
+        MM_LAUNCH_CHECK();
+        return MM_OK;
+    }
     if (a.mode == PRE_KU_G) {
         TraceScope tr(KC_SPLIT, s);
         split_pairs_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.U, Up, a.N);
