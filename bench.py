@@ -432,7 +432,8 @@ def ours(args):
         api.expint_step(plan, p.scheme, U, 1, t0=k * p.tau, g=g, ws=ws)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, events per step, L2 flushed between steps ----
+    # ---- timed region: K steps (each one replay of the step's captured graph),
+    # events per step, L2 flushed between steps; launches counted ----
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -440,7 +441,7 @@ def ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    api.trace_enable(True)
+    api.trace_enable(False)
     for k in range(args.steps):
         flush.fill_(k & 0xff)
         starts[k].record(stream)
@@ -450,12 +451,23 @@ def ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    launches = {c: api.trace_read(c) for c in (api.KC_CONTRACT_FP64, api.KC_CONTRACT_TF32,
-                                              api.KC_PREPASS, api.KC_SPLIT)}
-    api.trace_enable(False)
+    counts = {c: api.trace_read(c, timed=False)[0] for c in (api.KC_CONTRACT_FP64, api.KC_CONTRACT_TF32,
+                                                             api.KC_PREPASS, api.KC_SPLIT)}
     assert plan.status() == 0, "non-finite state during the timed steps"
     t_ms = parallel.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device="cuda")
     value = parallel.job_throughput([N * args.steps] * world, t_ms / 1e3)
+
+    # ---- per-kernel device times: the same steps launched directly, each launch
+    # bracketed by events on its stream (a graph replay has no per-kernel events) ----
+    ksteps = min(args.steps, 10)
+    api.trace_enable(True)
+    for k in range(ksteps):
+        flush.fill_(k & 0xff)
+        api.expint_step(plan, p.scheme, U, 1, t0=(args.warmup + args.steps + k) * p.tau, g=g, ws=ws)
+    torch.cuda.synchronize()
+    launches = {c: api.trace_read(c) for c in (api.KC_CONTRACT_FP64, api.KC_CONTRACT_TF32,
+                                              api.KC_PREPASS, api.KC_SPLIT)}
+    api.trace_enable(False)
 
     # ---- e2e: pinned host state in, one step, state out, every step ----
     U_host = torch.from_numpy(np.ascontiguousarray(p.u0)).pin_memory()
@@ -487,7 +499,7 @@ def ours(args):
     n_launch, k_ms = launches[kc]
     flops_per_launch = 2.0 * N * (sum(p.n) / len(p.n))   # 2 N n_mu per mode product
     achieved = flops_per_launch / (k_ms / n_launch / 1e3) / 1e12 if n_launch else None
-    total_launches = sum(v[0] for v in launches.values())
+    total_launches = sum(counts.values())
     if tf32:
         peaks = {}
         try:
@@ -505,7 +517,8 @@ def ours(args):
                 "traffic": profile_traffic("contract_tf32", args.workload),
                 "kernel": "tf32x3_mode_kernel (tcgen05 mu-mode contraction)",
                 "launches": n_launch, "avg_launch_ms": k_ms / n_launch if n_launch else None,
-                "share_of_step_time": k_ms / t_ms if t_ms else None,
+                "share_of_step_time": (k_ms / ksteps) / (t_ms / args.steps) if t_ms else None,
+                "timing": f"eager traced run of {ksteps} steps (the timed steps replay a CUDA graph)",
                 "flops_per_launch": tflops,
                 "peak_note": (f"TF32 dense peak = measured bf16 {bf16:.1f} TFLOP/s (MEASURED_PEAKS.json) "
                               "x nominal TF32/BF16 ratio 1.1/2.25") if args.prec == "tf32x3" else
@@ -516,7 +529,8 @@ def ours(args):
                 "traffic": profile_traffic("contract_fp64", args.workload),
                 "kernel": "dgemm_kernel (FP64 mu-mode contraction)",
                 "launches": n_launch, "avg_launch_ms": k_ms / n_launch if n_launch else None,
-                "share_of_step_time": k_ms / t_ms if t_ms else None,
+                "share_of_step_time": (k_ms / ksteps) / (t_ms / args.steps) if t_ms else None,
+                "timing": f"eager traced run of {ksteps} steps (the timed steps replay a CUDA graph)",
                 "flops_per_launch": flops_per_launch,
                 "peak_note": "FP64 peak derived: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 "
                              f"TFLOP/s); cuBLAS DGEMM measured {CUBLAS_DGEMM_TFLOPS_MEASURED} TFLOP/s"}
@@ -536,13 +550,14 @@ def ours(args):
         "e2e": {"value": e2e_value, "unit": METRIC, "steps": e2e_steps,
                 "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
         "gpu_launches": total_launches,
-        "kernel_ms_per_step": {"contract": k_ms / args.steps,
-                               "prepass": launches[api.KC_PREPASS][1] / args.steps,
-                               "split_update": launches[api.KC_SPLIT][1] / args.steps},
-        "launches_by_kernel": {"contract_fp64": launches[api.KC_CONTRACT_FP64][0],
-                               "contract_tf32": launches[api.KC_CONTRACT_TF32][0],
-                               "prepass": launches[api.KC_PREPASS][0],
-                               "split": launches[api.KC_SPLIT][0]},
+        "kernel_ms_per_step": {"contract": k_ms / ksteps,
+                               "prepass": launches[api.KC_PREPASS][1] / ksteps,
+                               "split_update": launches[api.KC_SPLIT][1] / ksteps},
+        "launches_by_kernel": {"contract_fp64": counts[api.KC_CONTRACT_FP64],
+                               "contract_tf32": counts[api.KC_CONTRACT_TF32],
+                               "prepass": counts[api.KC_PREPASS],
+                               "split": counts[api.KC_SPLIT]},
+        "graph": "each timed step is one replay of the step's captured CUDA graph",
         "clocks": clk,
     }
 

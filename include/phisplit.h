@@ -192,10 +192,19 @@ MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
  * The ell_max of the plan must cover the scheme (ETD2RK: 2, exp. Euler: 1,
  * Lawson: 0).  A non-finite value in the updated state raises
  * MM_STATUS_NONFINITE in the plan's status word.
+ * Graphs: unless turned off (phi_plan_set_graphs), the first call with a given
+ * (scheme, g's contents, U, ws, nsteps[, t0 for a time-dependent g]) captures the
+ * nsteps steps into a CUDA graph on a stream of the plan, and every call with the
+ * same arguments replays it on `stream` (one launch of host work).  The plan keeps
+ * the eight most recent graphs.  Calls made while `stream` is being captured, or
+ * while event tracing is on (mm_trace_enable(1)), launch the kernels directly.
  * Errors: MM_ERR_ARG, MM_ERR_UNSUPPORTED, MM_ERR_WORKSPACE, MM_ERR_CUDA.
  */
 MM_API int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,
                 int nsteps, void* ws, size_t ws_bytes, void* stream);
+
+/* Turn the graph capture and replay of expint_step on (default) or off.  Host only. */
+MM_API int phi_plan_set_graphs(mm_plan p, int on);
 
 /* ---- allocation-free Tucker chain ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers of

@@ -33,7 +33,7 @@ PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3, "bf16x3": MM_BF16X3}
 
 EXPORTS = ("phi_plan_create", "phi_plan_destroy", "phi_plan_info", "phi_plan_get_phi",
            "phi_plan_status", "mumode_workspace_bytes", "mumode_phi_apply",
-           "expint_workspace_bytes", "expint_step", "mm_status_str", "mm_version",
+           "expint_workspace_bytes", "expint_step", "phi_plan_set_graphs", "mm_status_str", "mm_version",
            "mm_trace_enable", "mm_trace_read", "tucker_apply_noalloc",
            "expint_batch_create", "expint_batch_run", "expint_batch_status", "expint_batch_info",
            "expint_batch_destroy", "expint_batched", "mm_batch_tile_plan")
@@ -84,6 +84,7 @@ def lib():
     L.expint_workspace_bytes.argtypes = [vp, i32, ctypes.POINTER(Nonlin)]
     L.expint_workspace_bytes.restype = sz
     L.expint_step.argtypes = [vp, i32, ctypes.POINTER(Nonlin), vp, f64, i32, vp, sz, vp]
+    L.phi_plan_set_graphs.argtypes = [vp, i32]
     L.mm_status_str.argtypes = [i32]
     L.mm_status_str.restype = ctypes.c_char_p
     L.mm_version.argtypes = []
@@ -187,6 +188,10 @@ class Plan:
 
     def status(self, reset: bool = True) -> int:
         return _check(lib().phi_plan_status(self.handle, int(reset), _stream()), "phi_plan_status")
+
+    def set_graphs(self, on: bool) -> None:
+        """expint_step replays captured CUDA graphs (default) or launches directly."""
+        _check(lib().phi_plan_set_graphs(self.handle, int(on)), "phi_plan_set_graphs")
 
 
 def mumode_workspace(plan: Plan) -> torch.Tensor:

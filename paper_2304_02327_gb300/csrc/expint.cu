@@ -6,12 +6,17 @@
 // between two N-double buffers; the last mode's epilogue performs the
 // integrator's update in FP64 (U+ = U + tau*Y, the ETD2RK stage values and
 // g(U2) - g(U)), so no separate elementwise pass touches HBM.
+//
+// expint_step captures its nsteps steps once per argument set into a CUDA graph
+// (on a stream of the plan) and replays it, so a call costs one graph launch of
+// host time whatever the number of kernels.
 #include <math.h>
 #include <string.h>
 
 #include "plan.cuh"
 #include "stencil.cuh"
 #include "tf32.cuh"
+#include "trace.cuh"
 
 namespace mm {
 
@@ -160,6 +165,75 @@ int scheme_ell(int scheme) {
 
 using namespace mm;
 
+namespace {
+
+int run_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, int nsteps, void* ws,
+              cudaStream_t s);
+
+bool same_nonlin(const mm_nonlin* a, int has_a, const mm_nonlin& b, int has_b) {
+    if (has_a != has_b) return false;
+    if (!has_a) return true;
+    if (a->kind != b.kind || a->B != b.B || a->C != b.C || a->psi_a != b.psi_a || a->psi_b != b.psi_b)
+        return false;
+    for (int i = 0; i < 4; ++i)
+        if (a->c[i] != b.c[i]) return false;
+    return true;
+}
+
+// The cached graph for these arguments, if any.
+const mm_graph_cache* find_graph(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, int nsteps,
+                                 void* ws) {
+    const bool tdep = g && g->kind == MM_G_ADR_MANUFACTURED;
+    for (const auto& e : p->graphs)
+        if (e.scheme == scheme && e.nsteps == nsteps && e.U == U && e.ws == ws && same_nonlin(g, g != nullptr, e.g, e.has_g) &&
+            (!tdep || e.t0 == t0))
+            return &e;
+    return nullptr;
+}
+
+// Capture the nsteps steps on the plan's own stream into a new cache entry (the
+// oldest of more than eight is dropped).
+int capture_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, int nsteps, void* ws) {
+    if (!p->cap && cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        p->cap = nullptr;
+        return MM_ERR_CUDA;
+    }
+    mm_graph_cache e;
+    e.scheme = scheme; e.nsteps = nsteps; e.U = U; e.ws = ws; e.t0 = t0;
+    e.has_g = g != nullptr;
+    if (g) e.g = *g;
+    trace_capture_begin();
+    if (cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        trace_capture_end(e.launches);
+        return MM_ERR_CUDA;
+    }
+    const int rc = run_steps(p, scheme, g, U, t0, nsteps, ws, p->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(p->cap, &graph);
+    trace_capture_end(e.launches);
+    if (rc || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc ? rc : MM_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return MM_ERR_CUDA;
+    if (p->graphs.size() >= 8) {
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back(e);
+    return MM_OK;
+}
+
+}  // namespace
+
+extern "C" int phi_plan_set_graphs(mm_plan p, int on) {
+    if (!p) return MM_ERR_ARG;
+    p->use_graphs = on != 0;
+    return MM_OK;
+}
+
 extern "C" size_t mumode_workspace_bytes(mm_plan p) {
     if (!p) return 0;
     if (p->prec != MM_FP64) return mixed_mumode_workspace_bytes(p);
@@ -230,8 +304,28 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     const size_t bytes = (size_t)p->N * sizeof(double);
     if (overlaps(ws, need, U, bytes)) return MM_ERR_ARG;
     if (nsteps == 0) return MM_OK;
-
     cudaStream_t s = (cudaStream_t)stream;
+    if (!p->use_graphs || trace_timing_on()) return run_steps(p, scheme, g, U, t0, nsteps, ws, s);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return run_steps(p, scheme, g, U, t0, nsteps, ws, s);      // the caller is capturing
+    const mm_graph_cache* e = find_graph(p, scheme, g, U, t0, nsteps, ws);
+    if (!e) {
+        int rc = capture_steps(p, scheme, g, U, t0, nsteps, ws);
+        if (rc) return rc;
+        e = &p->graphs.back();
+    }
+    MM_CUDA_TRY(cudaGraphLaunch(e->exec, s));
+    for (int c = 0; c < MM_KC_COUNT; ++c) trace_count(c, e->launches[c]);
+    return MM_OK;
+}
+
+namespace {
+
+// The body of expint_step after its argument checks (nsteps >= 1).
+int run_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, int nsteps, void* ws,
+              cudaStream_t s) {
+    const int gk = g ? g->kind : MM_G_NONE;
     if (p->prec != MM_FP64) {
         return mixed_expint(p, scheme, g, U, t0, nsteps, (uint8_t*)ws, s);
     }
@@ -317,3 +411,5 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     }
     return rc;
 }
+
+}  // namespace

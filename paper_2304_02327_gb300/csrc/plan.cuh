@@ -5,11 +5,17 @@
 
 #include "common.cuh"
 
+// One captured run of expint_step: the CUDA graph of its nsteps steps, valid for
+// exactly these arguments (every pointer and coefficient is baked into the nodes).
 struct mm_graph_cache {
     cudaGraphExec_t exec = nullptr;
-    int scheme = -1;
-    const void* key[8] = {};
-    double t0 = 0.0;
+    int scheme = -1, nsteps = 0;
+    const void* U = nullptr;
+    const void* ws = nullptr;
+    mm_nonlin g{};
+    int has_g = 0;
+    double t0 = 0.0;                   // part of the key only for a time-dependent g
+    long long launches[MM_KC_COUNT] = {};
 };
 
 struct mm_plan_s {
@@ -31,6 +37,9 @@ struct mm_plan_s {
     float* coef3f[MM_MAX_D] = {};      // mixed K u stencil: [a | c | row sum] per direction
     float* rem_split[MM_MAX_D] = {};   // mixed, dense A (d = 2): parts of A_mu minus its band
     unsigned int* status = nullptr;    // device status word (MM_STATUS_* bits)
+    int use_graphs = 1;                // expint_step replays captured graphs
+    cudaStream_t cap = nullptr;        // capture stream of those graphs
+    std::vector<mm_graph_cache> graphs;
     std::vector<void*> owned;
 
     bool alloc(void** p, size_t bytes) {
@@ -39,6 +48,9 @@ struct mm_plan_s {
         return true;
     }
     ~mm_plan_s() {
+        for (auto& e : graphs)
+            if (e.exec) cudaGraphExecDestroy(e.exec);
+        if (cap) cudaStreamDestroy(cap);
         for (void* q : owned) cudaFree(q);
         if (status) cudaFree(status);
     }

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(StencilArgsMixed a) {
 }
 
 constexpr int kT2 = 16;      // i_2 extent of a 3D tile
-constexpr int kZ = 32;       // planes per block of the 3D march
+constexpr int kZ = 32;       // most planes per block of the 3D march
 constexpr int kHalo3 = (kT2 + 2) * (kT1 + 2);      // 612 values of a plane with its halo
 constexpr int kPer3 = (kHalo3 + 255) / 256;         // of them per thread
 
@@ -192,18 +192,20 @@ __device__ __forceinline__ float stencil_term(float a, float2 nb, float uh, floa
     return fmaf(a, (nb.x - uh) + (nb.y - ul), acc);
 }
 
-__global__ void __launch_bounds__(256, 4) stencil3d_kernel(StencilArgsMixed a) {
+// zc planes per block (<= kZ): small grids march in shorter chunks so that every SM
+// gets blocks.
+__global__ void __launch_bounds__(256, 4) stencil3d_kernel(StencilArgsMixed a, int zc) {
     __shared__ float2 sp[3][kT2 + 2][kT1 + 2];
     const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = (int)a.n[2];
-    const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT2 - 1) / kT2, tz = (n3 + kZ - 1) / kZ;
+    const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT2 - 1) / kT2, tz = (n3 + zc - 1) / zc;
     const int64_t plane = (int64_t)n1 * n2;
     const float* cf1 = a.coef[0];
     const float* cf2 = a.coef[1];
     const float* cf3 = a.coef[2];
     const int c = threadIdx.x % kT1;
     for (int T = blockIdx.x; T < t1 * t2 * tz; T += gridDim.x) {
-        const int a1 = (T % t1) * kT1, a2 = ((T / t1) % t2) * kT2, z0 = (T / (t1 * t2)) * kZ;
-        const int z1 = min(n3, z0 + kZ);
+        const int a1 = (T % t1) * kT1, a2 = ((T / t1) % t2) * kT2, z0 = (T / (t1 * t2)) * zc;
+        const int z1 = min(n3, z0 + zc);
         // this thread's share of a plane's halo region: offsets, validity
         int64_t goff[kPer3];
         bool gin[kPer3];
@@ -305,13 +307,22 @@ int launch_prepass_mixed(const StencilArgsMixed& a0, float2* Up, cudaStream_t s)
     StencilArgsMixed a = a0;
     if (a.mode == PRE_KU_G && (a.d == 2 || a.d == 3)) {
         const int64_t t1 = (a.n[0] + kT1 - 1) / kT1;
-        const int64_t tiles = a.d == 2 ? t1 * ((a.n[1] + kT1 - 1) / kT1)
-                                       : t1 * ((a.n[1] + kT2 - 1) / kT2) * ((a.n[2] + kZ - 1) / kZ);
+        const int64_t target = (int64_t)num_sms() * 8;
+        int zc = kZ;
+        int64_t tiles;
+        if (a.d == 2) {
+            tiles = t1 * ((a.n[1] + kT1 - 1) / kT1);
+        } else {
+            const int64_t t12 = t1 * ((a.n[1] + kT2 - 1) / kT2);
+            const int64_t want_tz = (target + t12 - 1) / t12;            // chunks to fill the SMs
+            zc = (int)std::max<int64_t>(4, std::min<int64_t>(kZ, (a.n[2] + want_tz - 1) / want_tz));
+            tiles = t12 * ((a.n[2] + zc - 1) / zc);
+        }
         if (tiles > 0x7fffffffLL) return MM_ERR_SHAPE;
-        const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)num_sms() * 8);
+        const unsigned grid = (unsigned)std::min<int64_t>(tiles, target);
         TraceScope tr(KC_PREPASS, s);
         if (a.d == 2) stencil2d_kernel<<<grid, 256, 0, s>>>(a);
-        else stencil3d_kernel<<<grid, 256, 0, s>>>(a);
+        else stencil3d_kernel<<<grid, 256, 0, s>>>(a, zc);
         MM_LAUNCH_CHECK();
         return MM_OK;
     }

@@ -543,14 +543,23 @@ int fill_class(TcClass& k, const TcClassSpec& c, const Geometry& geo) {
     return rc;
 }
 
+// The kernels' shared-memory attribute, set once per process (outside any stream
+// capture: plan creation and batch creation call it first).
 template <class F, int C>
-int launch_group(TcGroup<C>& g, int64_t ctas, cudaStream_t s) {
+int configure_kernel() {
     static bool configured = false;
     if (!configured) {
         MM_CUDA_TRY(cudaFuncSetAttribute(tc_mode_kernel<F, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemLimit));
         configured = true;
     }
+    return MM_OK;
+}
+
+template <class F, int C>
+int launch_group(TcGroup<C>& g, int64_t ctas, cudaStream_t s) {
+    int rc0 = configure_kernel<F, C>();
+    if (rc0) return rc0;
     int stages;
     size_t smem;
     int rc = stages_for<F>(g.stage_nc, &stages, &smem);
@@ -677,6 +686,10 @@ int tc_group_product(int prec, const TcClassSpec* cls, int ncls, const int* nc_c
 
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s) {
     if (!encode_fn()) return MM_ERR_UNSUPPORTED;
+    int rc0 = p->prec == MM_BF16X3 ? configure_kernel<FormBF16, 1>() : configure_kernel<FormTF32, 1>();
+    if (!rc0) rc0 = p->prec == MM_BF16X3 ? configure_kernel<FormBF16, kMaxClasses>()
+                                         : configure_kernel<FormTF32, kMaxClasses>();
+    if (rc0) return rc0;
     for (int mu = 0; mu < p->d; ++mu) {
         if (p->owner[mu] != mu) {
             for (int l = 0; l <= p->ell_max; ++l) p->phi_split[mu][l] = p->phi_split[p->owner[mu]][l];

@@ -18,14 +18,35 @@ size_t g_used = 0;
 
 }  // namespace
 
+thread_local bool t_capturing = false;
+thread_local long long t_cap[KC_COUNT] = {};
+
 void trace_count(int cls, long long n) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_launches[cls] += n;
 }
 
+void trace_capture_begin() {
+    t_capturing = true;
+    for (int c = 0; c < KC_COUNT; ++c) t_cap[c] = 0;
+}
+
+void trace_capture_end(long long* counts) {
+    t_capturing = false;
+    for (int c = 0; c < KC_COUNT; ++c) counts[c] = t_cap[c];
+}
+
+bool trace_timing_on() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_on;
+}
+
 TraceScope::TraceScope(int cls, cudaStream_t s) : cls_(cls), s_(s), slot_(-1) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        if (t_capturing) t_cap[cls]++;
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
     g_launches[cls]++;
     if (!g_on) return;

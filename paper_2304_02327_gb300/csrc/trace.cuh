@@ -19,6 +19,12 @@ enum KernelClass : int {
 // timed (their graph's launches are counted with trace_count).
 // Adds n launches of class cls that ran inside a CUDA graph (counted, not timed).
 void trace_count(int cls, long long n);
+// Launches recorded into a stream capture by this host thread between begin and end
+// are tallied per class into counts[MM_KC_COUNT] (so each replay can be counted).
+void trace_capture_begin();
+void trace_capture_end(long long* counts);
+// True while launches are being timed with events (graph replay would hide them).
+bool trace_timing_on();
 
 class TraceScope {
 public:

@@ -197,3 +197,15 @@ def test_error_codes(api):
     with pytest.raises(api.PhisplitError) as e:        # V and P overlap
         api.mumode_phi_apply(plan, 0, U, P=U)
     assert e.value.code == -1
+
+
+def test_graph_replay_equals_direct_launches_fp64(api):
+    p = wl.adr_3d(seed=5, steps=3, scheme=wl.ETD2RK, sizes=(20, 17, 13))
+    plan, g, U = api.setup(p, "fp64")
+    for k in range(3):
+        api.expint_step(plan, p.scheme, U, 1, t0=k * p.tau, g=g)
+    plan2, g2, V = api.setup(p, "fp64")
+    plan2.set_graphs(False)
+    api.expint_step(plan2, p.scheme, V, 3, g=g2)
+    torch.cuda.synchronize()
+    assert torch.equal(U, V)

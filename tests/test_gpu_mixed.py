@@ -218,3 +218,23 @@ def test_mixed_riccati_n2048_sampled_last_step(api, form):
     # The stiff modes damp what earlier steps got wrong (the whole 50-step run lands
     # at 3.5e-7), so a single step is held to a tenth of the run's tolerance.
     assert err <= TOL_STEP / 10, err
+
+
+def test_graph_replay_equals_direct_launches(api, form):
+    """expint_step replays a captured graph by default; repeated calls (and calls on a
+    second state with the same plan, which need their own graph) must give exactly the
+    results of direct launches."""
+    p = wl.adr_3d(seed=5, steps=4, scheme=wl.ETD2RK, sizes=(40, 33, 24))
+    plan, g, U = api.setup(p, form)
+    U2 = U.clone()
+    ws = api.expint_workspace(plan, p.scheme, g)
+    for k in range(4):                       # one capture, three replays
+        api.expint_step(plan, p.scheme, U, 1, t0=k * p.tau, g=g, ws=ws)
+    api.expint_step(plan, p.scheme, U2, 2, g=g, ws=ws)   # another key: nsteps, state
+    api.expint_step(plan, p.scheme, U2, 2, t0=2 * p.tau, g=g, ws=ws)
+    torch.cuda.synchronize()
+    plan2, g2, V = api.setup(p, form)
+    plan2.set_graphs(False)
+    api.expint_step(plan2, p.scheme, V, 4, g=g2)
+    torch.cuda.synchronize()
+    assert torch.equal(U, V) and torch.equal(U2, V)
