@@ -78,6 +78,7 @@ extern "C" {
 #define MM_ETD2RK       1   /* eq. (12) / tensor form eq. (20)               */
 #define MM_LAWSON_EULER 2   /* eq. (9)  / tensor form eq. (17)               */
 #define MM_LAWSON2B     3   /* eq. (10) / tensor form eq. (18)               */
+#define MM_EXPROSEULER  4   /* eq. (13) / tensor form eq. (21): Riccati G, FP64 */
 
 /* ---- nonlinearity g(t, u) (eq. (1a)) ----------------------------------- */
 #define MM_G_NONE            0  /* g = 0                                         */
@@ -177,6 +178,12 @@ MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
  *                   U+ = U2 + tau P_2^(2)(G(t + tau, U2) - G(t, U))       eq. (20)
  *   MM_LAWSON_EULER U+ = (U + tau G(t, U)) x_mu e^{tau A_mu}              eq. (17)
  *   MM_LAWSON2B     eq. (18)
+ *   MM_EXPROSEULER  U+ = U + tau (K U + G(U)) x_1 phi_1(tau J_1) x_2 phi_1(tau J_2),
+ *                   J_1 = A_1 + U B, J_2 = A_2 + (B U)^T: the Riccati term's
+ *                   Jacobian at U (Section 4.1, eq. (21)), phi_1 formed on the GPU
+ *                   every step in FP64 (plan form MM_FP64 only; the scaling is chosen
+ *                   on the host, so each step synchronises `stream` and the steps are
+ *                   launched directly, never replayed from a graph)
  * P_l^(2) carries the (l!)^(d-1) factor of Theorem 1 (so the phi_2 stage of
  * ETD2RK is scaled by 2^(d-1)), and tau multiplies both K U and G in the first
  * stage, as the vector forms eq. (11)-(12) require.

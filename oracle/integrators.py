@@ -14,6 +14,10 @@ Tensor formulations of Section 3.2 with tensors in the (n_d, ..., n_1) layout:
 * Lawson2b (eq. (18)):
       U2 = (U + tau G(U)) x_mu e^{tau A_mu}
       U+ = (U + tau/2 G(U)) x_mu e^{tau A_mu} + tau/2 G(U2)
+* exponential Rosenbrock-Euler (eq. (13), tensor form eq. (21), read like eq. (20)
+  with tau on both K U and G), for the Riccati term only, whose Jacobian at U_n is
+  again a Kronecker sum (Section 4.1): J_1 = A_1 + U_n B, J_2 = A_2 + (B U_n)^T and
+      U+ = U + tau * (K U + G(U)) x_1 phi_1(tau J_1) x_2 phi_1(tau J_2)
 
 g may depend on t only through the manufactured forcing of the paper's ADR test
 (Section 4.2): g(t, u) = 1/(1 + u^2) + e^t a - 1/(1 + e^{2t} b^2), with the
@@ -31,7 +35,7 @@ from .phi import phi_matrices
 from .tucker import mode_product, phisplit_apply
 
 G_NONE, G_CUBIC, G_RICCATI, G_ADR_MANUFACTURED = 0, 1, 2, 3
-EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B = 0, 1, 2, 3
+EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B, EXPROSEULER = 0, 1, 2, 3, 4
 
 
 @dataclasses.dataclass
@@ -91,6 +95,13 @@ def g_eval(op: OracleProblem, U: np.ndarray, t: float = 0.0) -> np.ndarray:
     raise ValueError(f"unknown g kind {op.g_kind}")
 
 
+def riccati_jacobian(op: OracleProblem, U: np.ndarray) -> List[np.ndarray]:
+    """[J_1, J_2] with K + dG(U) = J_2 (+) J_1 for G(U) = C + U B U (Section 4.1):
+    the derivative V B U + U B V of U B U adds U B to A_1 and (B U)^T to A_2."""
+    Um = U.T                      # stored arrays are (n_2, n_1): the transposes
+    return [op.A[0] + Um @ op.B, op.A[1] + (op.B @ Um).T]
+
+
 def step(op: OracleProblem, U: np.ndarray, scheme: int, t: float = 0.0) -> np.ndarray:
     """One step of size op.tau from (t, U) (Section 3.2 tensor formulations)."""
     tau = op.tau
@@ -110,6 +121,12 @@ def step(op: OracleProblem, U: np.ndarray, scheme: int, t: float = 0.0) -> np.nd
         U2 = phisplit_apply(U + tau * Gn, op.phi_list(0), 0)
         return (phisplit_apply(U + 0.5 * tau * Gn, op.phi_list(0), 0)
                 + 0.5 * tau * g_eval(op, U2, t + tau))
+    if scheme == EXPROSEULER:
+        if op.g_kind != G_RICCATI:
+            raise ValueError("exponential Rosenbrock-Euler needs the Riccati term")
+        W = kron_apply(U, op.A) + g_eval(op, U, t)
+        phis = [phi_matrices(tau * J, 1)[1] for J in riccati_jacobian(op, U)]
+        return U + tau * phisplit_apply(W, phis, 1)
     raise ValueError(f"unknown scheme {scheme}")
 
 

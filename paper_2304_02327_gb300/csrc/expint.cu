@@ -41,25 +41,46 @@ double factorial(int k) {
     return f;
 }
 
-int fp64_mode_product(mm_plan_s* p, int ell, int mu, const double* in, const Epi& e, cudaStream_t s) {
-    Gemm g = mode_gemm(p->d, p->n, mu, p->phi[mu - 1][ell], in);
-    return launch_dgemm(g, e, s);
+// FP64 Tucker chain with the matrices M[0..d-1]: modes 1..d-1 store into
+// outs[0..d-2]; mode d applies `last`.
+int fp64_chain_m(mm_plan_s* p, const double* const* M, const double* in, double* const* outs, const Epi& last,
+                 cudaStream_t s) {
+    const double* cur = in;
+    for (int mu = 1; mu <= p->d; ++mu) {
+        Epi e{};
+        if (mu < p->d) {
+            e.kind = EPI_STORE;
+            e.alpha = 1.0;
+            e.C = outs[mu - 1];
+        } else {
+            e = last;
+        }
+        int rc = launch_dgemm(mode_gemm(p->d, p->n, mu, M[mu - 1], cur), e, s);
+        if (rc) return rc;
+        cur = mu < p->d ? outs[mu - 1] : nullptr;
+    }
+    return MM_OK;
 }
 
-// FP64 Tucker chain: modes 1..d-1 store into outs[0..d-2]; mode d applies `last`.
+// The same with the plan's phi_ell(tau A_mu).
 int fp64_chain(mm_plan_s* p, int ell, const double* in, double* const* outs, const Epi& last,
                cudaStream_t s) {
-    const double* cur = in;
-    for (int mu = 1; mu < p->d; ++mu) {
-        Epi e{};
-        e.kind = EPI_STORE;
-        e.alpha = 1.0;
-        e.C = outs[mu - 1];
-        int rc = fp64_mode_product(p, ell, mu, cur, e, s);
-        if (rc) return rc;
-        cur = outs[mu - 1];
+    const double* M[MM_MAX_D];
+    for (int mu = 0; mu < p->d; ++mu) M[mu] = p->phi[mu][ell];
+    return fp64_chain_m(p, M, in, outs, last, s);
+}
+
+// J = A + X (n*n elements) and J = A + T^T (n x n): the Riccati Jacobian's directions.
+__global__ void add_kernel(const double* __restrict__ A, const double* __restrict__ X, double* J, int64_t nn) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+        J[i] = A[i] + X[i];
+}
+__global__ void add_transpose_kernel(const double* __restrict__ A, const double* __restrict__ T, double* J, int n) {
+    const int64_t nn = (int64_t)n * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i % n, c = i / n;
+        J[i] = A[i] + T[c + (int64_t)n * r];
     }
-    return fp64_mode_product(p, ell, p->d, cur, last, s);
 }
 
 // Tucker of `in` (consumable, N doubles) with scratch (N doubles) and the final
@@ -143,6 +164,14 @@ int ku_plus_g(mm_plan_s* p, const mm_nonlin* g, const double* U, double t, doubl
     return MM_OK;
 }
 
+// Rosenbrock-Euler (d = 2) workspace beyond the Riccati pieces, in doubles:
+// J1 (n1^2), J2 and B U (n2^2 each), phi_0 and phi_1 of both directions, the
+// phi formation's scratch (4 nmax^2), its column sums (nmax) and band word.
+size_t rosenbrock_extra(const mm_plan_s* p) {
+    const size_t n1 = (size_t)p->n[0], n2 = (size_t)p->n[1], nm = n1 > n2 ? n1 : n2;
+    return 3 * n1 * n1 + 4 * n2 * n2 + 4 * nm * nm + nm + 2;
+}
+
 bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
     const char* x = (const char*)a;
     const char* y = (const char*)b;
@@ -155,6 +184,7 @@ int scheme_ell(int scheme) {
     case MM_ETD2RK: return 2;
     case MM_LAWSON_EULER: return 0;
     case MM_LAWSON2B: return 0;
+    case MM_EXPROSEULER: return 1;
     default: return -1;
     }
 }
@@ -282,6 +312,7 @@ extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin*
         const size_t n1 = (size_t)p->n[0];
         elems += N + (n1 * n1 > N ? n1 * n1 : N);  // Gn, XB
     }
+    if (scheme == MM_EXPROSEULER && p->d == 2) elems += rosenbrock_extra(p);
     return elems * sizeof(double);
 }
 
@@ -295,8 +326,9 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     if (gk < MM_G_NONE || gk > MM_G_ADR_MANUFACTURED) return MM_ERR_ARG;
     if (gk == MM_G_RICCATI) {
         if (p->d != 2 || !g->B || !g->C) return MM_ERR_ARG;
-        if (scheme != MM_EXPEULER && scheme != MM_ETD2RK) return MM_ERR_UNSUPPORTED;
+        if (scheme != MM_EXPEULER && scheme != MM_ETD2RK && scheme != MM_EXPROSEULER) return MM_ERR_UNSUPPORTED;
     }
+    if (scheme == MM_EXPROSEULER && (gk != MM_G_RICCATI || p->prec != MM_FP64)) return MM_ERR_UNSUPPORTED;
     if (gk == MM_G_ADR_MANUFACTURED && (!g->psi_a || !g->psi_b)) return MM_ERR_ARG;
     const size_t need = expint_workspace_bytes(p, scheme, g);
     const uintptr_t amask = p->prec == MM_FP64 ? 7 : 15;
@@ -305,7 +337,10 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     if (overlaps(ws, need, U, bytes)) return MM_ERR_ARG;
     if (nsteps == 0) return MM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!p->use_graphs || trace_timing_on()) return run_steps(p, scheme, g, U, t0, nsteps, ws, s);
+    // Rosenbrock-Euler forms phi of its Jacobian every step, choosing the scaling on
+    // the host: it runs with direct launches only
+    if (!p->use_graphs || trace_timing_on() || scheme == MM_EXPROSEULER)
+        return run_steps(p, scheme, g, U, t0, nsteps, ws, s);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return run_steps(p, scheme, g, U, t0, nsteps, ws, s);      // the caller is capturing
@@ -379,6 +414,39 @@ int run_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, i
             e2.kind = EPI_ETD_S2; e2.alpha = tau * pow(2.0, d - 1); e2.U = U; e2.U2 = U2;
             e2.status = p->status;
             rc = run_tucker(p, 2, W2, other, e2, s);
+            break;
+        }
+        case MM_EXPROSEULER: {
+            // W = K U + G(U) (and XB = U B), then J_1 = A_1 + U B, J_2 = A_2 + (B U)^T
+            rc = ku_plus_g(p, g, U, t, X, Gn, XB, s);
+            if (rc) break;
+            const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+            const int64_t q1 = (int64_t)n1 * n1, q2 = (int64_t)n2 * n2;
+            const int nm = n1 > n2 ? n1 : n2;
+            double* J1 = XB + (q1 > N ? q1 : N);
+            double* J2 = J1 + q1;
+            double* BU = J2 + q2;
+            double* P1[2] = {BU + q2, BU + q2 + q1};            // phi_0, phi_1 of J_1
+            double* P2[2] = {P1[1] + q1, P1[1] + q1 + q2};      // of J_2
+            double* scratch = P2[1] + q2;                        // 4 nm^2
+            // the pieces end at scratch + 4 nm^2 + nm + 2 doubles: rosenbrock_extra()
+            double* colsum = scratch + 4 * (int64_t)nm * nm;
+            int* band = (int*)(colsum + nm);
+            add_kernel<<<(unsigned)std::min<int64_t>((q1 + 255) / 256, 4096), 256, 0, s>>>(p->A[0], XB, J1, q1);
+            rc = plain_gemm(n2, n2, n1, g->B, n2, U, n1, BU, n2, nullptr, 0, nullptr, 0, s);
+            if (rc) break;
+            add_transpose_kernel<<<(unsigned)std::min<int64_t>((q2 + 255) / 256, 4096), 256, 0, s>>>(p->A[1], BU,
+                                                                                                   J2, n2);
+            if (cudaGetLastError() != cudaSuccess) { rc = MM_ERR_CUDA; break; }
+            int sq = 0, bw = 0;
+            rc = form_phis(n1, J1, tau, 1, P1, colsum, band, &sq, &bw, s, scratch);
+            if (!rc) rc = form_phis(n2, J2, tau, 1, P2, colsum, band, &sq, &bw, s, scratch);
+            if (rc) break;
+            const double* M[2] = {P1[1], P2[1]};
+            Epi e{};
+            e.kind = EPI_EE; e.alpha = tau; e.U = U; e.status = p->status;
+            double* outs[1] = {Y};
+            rc = fp64_chain_m(p, M, X, outs, e, s);
             break;
         }
         case MM_LAWSON_EULER: {

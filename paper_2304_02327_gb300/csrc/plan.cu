@@ -115,13 +115,19 @@ double fact(int k) {
     return f;
 }
 
+}  // namespace
+
 // phi_0..phi_L of X = tau*A (A column-major n x n on the device) into out[0..L].
+// scratch: (L + 3) n^2 doubles of device memory, or NULL to allocate them here.
 int form_phis(int n, const double* A, double tau, int L, double* const* out, double* colsum_dev,
-              int* band_dev, int* s_out, int* band_out, cudaStream_t s) {
+              int* band_dev, int* s_out, int* band_out, cudaStream_t s, double* scratch) {
     const int64_t nn = (int64_t)n * n;
     std::vector<double*> tmp(L + 3, nullptr);
-    for (auto& p : tmp) {
-        if (cudaMalloc(&p, nn * sizeof(double)) != cudaSuccess) {
+    const bool own = scratch == nullptr;
+    for (int i = 0; i < L + 3; ++i) {
+        if (!own) {
+            tmp[i] = scratch + i * nn;
+        } else if (cudaMalloc(&tmp[i], nn * sizeof(double)) != cudaSuccess) {
             for (auto q : tmp) if (q) cudaFree(q);
             return MM_ERR_NOMEM;
         }
@@ -190,11 +196,10 @@ int form_phis(int n, const double* A, double tau, int L, double* const* out, dou
         MM_CUDA_TRY(cudaStreamSynchronize(s));
     }
 done:
-    for (auto p : tmp) cudaFree(p);
+    if (own)
+        for (auto p : tmp) cudaFree(p);
     return rc;
 }
-
-}  // namespace
 
 }  // namespace mm
 
@@ -263,7 +268,7 @@ extern "C" int phi_plan_create(mm_plan* out, int d, const int64_t* n, const doub
             if (!p->alloc((void**)&p->phi[mu][l], nn * sizeof(double))) { rc = MM_ERR_NOMEM; goto fail; }
         int band = 0;
         rc = form_phis((int)n[mu], p->A[mu], tau, ell_max, p->phi[mu], colsum, flag + 1,
-                       &p->squarings[mu], &band, s);
+                       &p->squarings[mu], &band, s, nullptr);
         if (rc) goto fail;
         if (band > 1) p->tridiag = 0;
         extract_tridiag_kernel<<<grid_for(n[mu]), 256, 0, s>>>(p->A[mu], (int)n[mu], p->diag3[mu]);

@@ -59,4 +59,11 @@ struct mm_plan_s {
 namespace mm {
 // Builds the TF32x3 operand images of the plan's phi matrices (tf32.cu).
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s);
+// phi_0 .. phi_L of tau*A (n x n, column-major, device) into out[0..L] by scaling,
+// Taylor series and the squaring recurrence eq. (16) (plan.cu).  colsum_dev: n
+// doubles, band_dev: one int (device); *s_out receives the squarings, *band_out the
+// band width of A.  scratch: (L + 3) n^2 device doubles, or NULL to allocate.
+// Synchronises `s` (the scaling is chosen from the norm on the host).
+int form_phis(int n, const double* A, double tau, int L, double* const* out, double* colsum_dev,
+              int* band_dev, int* s_out, int* band_out, cudaStream_t s, double* scratch);
 }  // namespace mm

@@ -38,9 +38,10 @@ EXPEULER = 0    # exponential Euler, eq. (11); tensor form eq. (19)
 ETD2RK = 1      # ETD2RK, eq. (12); tensor form eq. (20)
 LAWSON_EULER = 2  # Lawson-Euler, eq. (9); tensor form eq. (17)
 LAWSON2B = 3    # Lawson2b, eq. (10); tensor form eq. (18)
+EXPROSEULER = 4  # exponential Rosenbrock-Euler, eq. (13); tensor form eq. (21) (Riccati)
 
 SCHEME_NAMES = {EXPEULER: "expeuler", ETD2RK: "etd2rk",
-                LAWSON_EULER: "lawson_euler", LAWSON2B: "lawson2b"}
+                LAWSON_EULER: "lawson_euler", LAWSON2B: "lawson2b", EXPROSEULER: "exprosenbrock"}
 
 
 @dataclasses.dataclass
@@ -152,6 +153,43 @@ def riccati_2d(n: int = 2048, seed: int = 5, tau: float = 1e-4, steps: int = 50,
     # States are stored as (n_2, n_1) arrays (i_1 fastest): U_store = U^T.
     return Problem(name=f"riccati_2d_n{n}", A=A, u0=np.zeros((n, n)),
                    g_kind=G_RICCATI, B=B, C=np.ascontiguousarray(Cm.T), tau=tau,
+                   steps=steps, scheme=scheme)
+
+
+def lq_riccati(nhat: int = 30, steps: int = 170, scheme: int = ETD2RK, T: float = 0.025,
+               alpha: float = 100.0) -> Problem:
+    """The paper's linear-quadratic control problem (Section 4.1), no random input.
+
+    A (n x n, n = nhat^2) discretises d_xx + d_yy - 10 x d_x - 100 y d_y on [0,1]^2
+    with homogeneous Dirichlet conditions by second-order centred differences on the
+    inner grid x_i = i h, h = 1/(nhat + 1), unknown k = i + (j - 1) nhat (x fastest);
+    b_k = 1 where 0.1 < x_i <= 0.3, c_k = 1 where 0.7 < x_i <= 0.9, C = alpha c^T c,
+    B = -b b^T, U0 = 0.  The Riccati equation U' = A^T U + U A + C + U B U is the
+    two-direction form with A_1 = A_2 = A^T; tau = T / steps.
+    """
+    h = 1.0 / (nhat + 1)
+    x = grid(nhat)
+    n = nhat * nhat
+    A = np.zeros((n, n))
+    for j in range(nhat):
+        for i in range(nhat):
+            k = i + j * nhat
+            A[k, k] = -4.0 / h ** 2
+            if i > 0:
+                A[k, k - 1] = 1.0 / h ** 2 + 10.0 * x[i] / (2 * h)
+            if i < nhat - 1:
+                A[k, k + 1] = 1.0 / h ** 2 - 10.0 * x[i] / (2 * h)
+            if j > 0:
+                A[k, k - nhat] = 1.0 / h ** 2 + 100.0 * x[j] / (2 * h)
+            if j < nhat - 1:
+                A[k, k + nhat] = 1.0 / h ** 2 - 100.0 * x[j] / (2 * h)
+    xi = np.tile(x, nhat)                                # x_i of unknown k
+    b = ((xi > 0.1) & (xi <= 0.3)).astype(np.float64)
+    c = ((xi > 0.7) & (xi <= 0.9)).astype(np.float64)
+    B = -np.outer(b, b)
+    Cm = alpha * np.outer(c, c)
+    return Problem(name=f"lq_riccati_nhat{nhat}", A=[A.T.copy(), A.T.copy()], u0=np.zeros((n, n)),
+                   g_kind=G_RICCATI, B=B, C=np.ascontiguousarray(Cm.T), tau=T / steps,
                    steps=steps, scheme=scheme)
 
 

@@ -209,3 +209,21 @@ def test_graph_replay_equals_direct_launches_fp64(api):
     api.expint_step(plan2, p.scheme, V, 3, g=g2)
     torch.cuda.synchronize()
     assert torch.equal(U, V)
+
+
+@pytest.mark.parametrize("scheme", [wl.EXPROSEULER, wl.ETD2RK])
+def test_lq_riccati_matches_oracle(api, scheme):
+    """The paper's LQ-control Riccati problem (Section 4.1, banded non-tridiagonal A)
+    at nhat = 12 (144 x 144 matrices), 10 steps; exponential Rosenbrock-Euler forms
+    phi_1 of its Jacobian on the GPU every step (eq. (21))."""
+    p = wl.lq_riccati(12, 10, scheme, T=0.025 * 10 / 170)
+    got, ref = run_pair(api, p)
+    assert rel_err_fro(got, ref) <= TOL and rel_err_inf(got, ref) <= TOL
+
+
+def test_rosenbrock_rejects_other_nonlinearities(api):
+    p = wl.allen_cahn_2d(n=16, seed=1, steps=1, scheme=wl.EXPEULER)
+    plan, g, U = api.setup(p, "fp64", ell_max=1)
+    with pytest.raises(api.PhisplitError) as e:
+        api.expint_step(plan, wl.EXPROSEULER, U, 1, g=g)
+    assert e.value.code == -3

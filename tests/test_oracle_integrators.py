@@ -130,3 +130,82 @@ def test_planted_missing_tau_breaks_consistency(monkeypatch):
         o = observed_orders(oi.ETD2RK, steps=(8, 16, 32))
     # either it diverges (nan/inf) or the error stops decreasing
     assert not (abs(o[-1] - 2) < 0.5), o
+
+
+def riccati_small(n1=6, n2=5, seed=3):
+    rng = np.random.default_rng(seed)
+    A = [wl.fd_matrix(n1, 0.3, 0.4), wl.fd_matrix(n2, 0.2, -0.3)]
+    B = 0.3 * rng.standard_normal((n2, n1))
+    C = 0.5 * rng.standard_normal((n2, n1))          # stored like U: (n2, n1)
+    U0 = 0.2 * rng.standard_normal((n2, n1))
+    return A, B, C, U0
+
+
+def riccati_rhs_vec(A, B, C, n1, n2):
+    """u' for the column-stacked matrix U (n1 x n2): A1 U + U A2^T + C + U B U."""
+    Cm = C.T
+
+    def f(t, u):
+        Um = u.reshape(n2, n1).T
+        return (A[0] @ Um + Um @ A[1].T + Cm + Um @ B @ Um).T.reshape(-1)
+    return f
+
+
+def test_riccati_jacobian_is_the_linearisation():
+    """K + dG(U) = J_2 (+) J_1: the Kronecker sum of the oracle's J matches a
+    finite-difference Jacobian of the Riccati right-hand side (Section 4.1)."""
+    n1, n2 = 6, 5
+    A, B, C, U0 = riccati_small(n1, n2)
+    op = OracleProblem(A=A, tau=0.1, g_kind=oi.G_RICCATI, B=B, C=C)
+    J = oi.riccati_jacobian(op, U0)
+    f = riccati_rhs_vec(A, B, C, n1, n2)
+    u0 = U0.reshape(-1)
+    h = 1e-6
+    fd = np.stack([(f(0, u0 + h * e) - f(0, u0 - h * e)) / (2 * h) for e in np.eye(n1 * n2)], axis=1)
+    assert np.abs(kron_sum(J) - fd).max() < 1e-7 * max(1.0, np.abs(fd).max())
+
+
+def test_rosenbrock_linear_problem_is_exponential_euler():
+    """B = 0: the Jacobian is K itself, so exponential Rosenbrock-Euler is exponential
+    Euler (eq. (13) with K_n = K), step for step."""
+    A, B, C, U0 = riccati_small()
+    op = OracleProblem(A=A, tau=0.05, g_kind=oi.G_RICCATI, B=0.0 * B, C=C)
+    op.ensure_phis(1)
+    a = oi.step(op, U0, oi.EXPROSEULER)
+    b = oi.step(op, U0, oi.EXPEULER)
+    assert np.abs(a - b).max() < 1e-14 * np.abs(b).max()
+
+
+def test_rosenbrock_observed_order_two():
+    """Exponential Rosenbrock-Euler (PHISPLIT) on a small Riccati problem: global order 2
+    on a step sweep against scipy's DOP853 on the assembled system, as the paper's
+    order table for the LQ problem shows (Section 4.1)."""
+    n1, n2 = 6, 5
+    A, B, C, U0 = riccati_small(n1, n2)
+    T = 0.4
+    f = riccati_rhs_vec(A, B, C, n1, n2)
+    ref = scipy.integrate.solve_ivp(f, (0, T), U0.reshape(-1), method="DOP853", rtol=1e-13,
+                                    atol=1e-14).y[:, -1]
+    errs = []
+    for m in (8, 16, 32, 64):
+        op = OracleProblem(A=A, tau=T / m, g_kind=oi.G_RICCATI, B=B, C=C)
+        errs.append(np.abs(integrate(op, U0, oi.EXPROSEULER, m).reshape(-1) - ref).max())
+    o = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert abs(o[-1] - 2) < 0.15, o
+
+
+def test_lq_riccati_reaches_the_algebraic_riccati_solution():
+    """The paper's LQ problem (Section 4.1) at a small grid: both second-order schemes
+    run to the steady state, the solution of A^T U + U A + C + U B U = 0, which scipy's
+    continuous algebraic Riccati solver gives independently (B = -b b^T, C = alpha c^T c)."""
+    nhat, T, steps = 6, 0.5, 100
+    p = wl.lq_riccati(nhat, steps, wl.ETD2RK, T=T)
+    A = p.A[0].T                                        # the system matrix
+    xi = np.tile(wl.grid(nhat), nhat)
+    b = ((xi > 0.1) & (xi <= 0.3)).astype(float)[:, None]
+    Cm = p.C.T
+    X = scipy.linalg.solve_continuous_are(A, b, Cm, np.eye(1))
+    for scheme in (oi.ETD2RK, oi.EXPROSEULER):
+        op = OracleProblem.from_problem(p, lmax=2)
+        U = integrate(op, p.u0, scheme, steps)
+        assert oi.rel_err_fro(U.T, X) < 1e-6, scheme
