@@ -79,6 +79,7 @@ extern "C" {
 #define MM_LAWSON_EULER 2   /* eq. (9)  / tensor form eq. (17)               */
 #define MM_LAWSON2B     3   /* eq. (10) / tensor form eq. (18)               */
 #define MM_EXPROSEULER  4   /* eq. (13) / tensor form eq. (21): Riccati G, FP64 */
+#define MM_EXPEULER_ALT 5   /* exp. Euler, alternative form (Section 3.2), FP64 */
 
 /* ---- nonlinearity g(t, u) (eq. (1a)) ----------------------------------- */
 #define MM_G_NONE            0  /* g = 0                                         */
@@ -178,6 +179,10 @@ MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
  *                   U+ = U2 + tau P_2^(2)(G(t + tau, U2) - G(t, U))       eq. (20)
  *   MM_LAWSON_EULER U+ = (U + tau G(t, U)) x_mu e^{tau A_mu}              eq. (17)
  *   MM_LAWSON2B     eq. (18)
+ *   MM_EXPEULER_ALT U+ = U x_mu e^{tau A_mu} + tau P_1^(2)(G(U)): the alternative
+ *                   form of Section 3.2, exact for linear autonomous problems (plan
+ *                   form MM_FP64 only: a mixed form would keep the whole new state, not
+ *                   an increment, at the split precision; pointwise g only)
  *   MM_EXPROSEULER  U+ = U + tau (K U + G(U)) x_1 phi_1(tau J_1) x_2 phi_1(tau J_2),
  *                   J_1 = A_1 + U B, J_2 = A_2 + (B U)^T: the Riccati term's
  *                   Jacobian at U (Section 4.1, eq. (21)), phi_1 formed on the GPU

@@ -14,6 +14,9 @@ Tensor formulations of Section 3.2 with tensors in the (n_d, ..., n_1) layout:
 * Lawson2b (eq. (18)):
       U2 = (U + tau G(U)) x_mu e^{tau A_mu}
       U+ = (U + tau/2 G(U)) x_mu e^{tau A_mu} + tau/2 G(U2)
+* exponential Euler, alternative form (Section 3.2, after eq. (19)), exact for
+  linear autonomous problems:
+      U+ = U x_mu e^{tau A_mu} + tau * G(U) x_1 phi_1(tau A_1) ... x_d phi_1(tau A_d)
 * exponential Rosenbrock-Euler (eq. (13), tensor form eq. (21), read like eq. (20)
   with tau on both K U and G), for the Riccati term only, whose Jacobian at U_n is
   again a Kronecker sum (Section 4.1): J_1 = A_1 + U_n B, J_2 = A_2 + (B U_n)^T and
@@ -35,7 +38,7 @@ from .phi import phi_matrices
 from .tucker import mode_product, phisplit_apply
 
 G_NONE, G_CUBIC, G_RICCATI, G_ADR_MANUFACTURED = 0, 1, 2, 3
-EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B, EXPROSEULER = 0, 1, 2, 3, 4
+EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B, EXPROSEULER, EXPEULER_ALT = 0, 1, 2, 3, 4, 5
 
 
 @dataclasses.dataclass
@@ -121,6 +124,9 @@ def step(op: OracleProblem, U: np.ndarray, scheme: int, t: float = 0.0) -> np.nd
         U2 = phisplit_apply(U + tau * Gn, op.phi_list(0), 0)
         return (phisplit_apply(U + 0.5 * tau * Gn, op.phi_list(0), 0)
                 + 0.5 * tau * g_eval(op, U2, t + tau))
+    if scheme == EXPEULER_ALT:
+        return (phisplit_apply(U, op.phi_list(0), 0)
+                + tau * phisplit_apply(g_eval(op, U, t), op.phi_list(1), 1))
     if scheme == EXPROSEULER:
         if op.g_kind != G_RICCATI:
             raise ValueError("exponential Rosenbrock-Euler needs the Riccati term")

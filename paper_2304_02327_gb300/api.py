@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "libphisplit.so")
 
 MM_OK = 0
 MM_FP64, MM_TF32X3, MM_BF16X3 = 0, 1, 2
-EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B, EXPROSEULER = 0, 1, 2, 3, 4
+EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B, EXPROSEULER, EXPEULER_ALT = 0, 1, 2, 3, 4, 5
 G_NONE, G_CUBIC, G_RICCATI, G_ADR_MANUFACTURED = 0, 1, 2, 3
 STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2
 PRECISIONS = {"fp64": MM_FP64, "tf32x3": MM_TF32X3, "bf16x3": MM_BF16X3}
@@ -277,7 +277,7 @@ def trace_read(cls: int, timed: bool = True):
 
 
 def ell_for_scheme(scheme: int) -> int:
-    return {EXPEULER: 1, ETD2RK: 2, LAWSON_EULER: 0, LAWSON2B: 0, EXPROSEULER: 1}[scheme]
+    return {EXPEULER: 1, ETD2RK: 2, LAWSON_EULER: 0, LAWSON2B: 0, EXPROSEULER: 1, EXPEULER_ALT: 1}[scheme]
 
 
 def setup(problem: "wl.Problem", prec: str = "fp64", ell_max: Optional[int] = None):

@@ -185,6 +185,7 @@ int scheme_ell(int scheme) {
     case MM_LAWSON_EULER: return 0;
     case MM_LAWSON2B: return 0;
     case MM_EXPROSEULER: return 1;
+    case MM_EXPEULER_ALT: return 1;
     default: return -1;
     }
 }
@@ -306,6 +307,7 @@ extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin*
     const size_t N = (size_t)p->N;
     size_t buffers = 2;                          // Tucker ping-pong X, Y
     if (scheme == MM_ETD2RK) buffers = 3;        // + U2
+    if (scheme == MM_EXPEULER_ALT) buffers = 3;  // + the first Tucker's result
     if (scheme == MM_LAWSON2B) buffers = 4;      // + Z, U2
     size_t elems = buffers * N;
     if (g && g->kind == MM_G_RICCATI && p->d == 2) {
@@ -329,6 +331,7 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
         if (scheme != MM_EXPEULER && scheme != MM_ETD2RK && scheme != MM_EXPROSEULER) return MM_ERR_UNSUPPORTED;
     }
     if (scheme == MM_EXPROSEULER && (gk != MM_G_RICCATI || p->prec != MM_FP64)) return MM_ERR_UNSUPPORTED;
+    if (scheme == MM_EXPEULER_ALT && (gk == MM_G_RICCATI || p->prec != MM_FP64)) return MM_ERR_UNSUPPORTED;
     if (gk == MM_G_ADR_MANUFACTURED && (!g->psi_a || !g->psi_b)) return MM_ERR_ARG;
     const size_t need = expint_workspace_bytes(p, scheme, g);
     const uintptr_t amask = p->prec == MM_FP64 ? 7 : 15;
@@ -369,7 +372,7 @@ int run_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, i
     double* Y = X + N;
     double* U2 = Y + N;                                     // ETD2RK, Lawson2b
     double* Z = (scheme == MM_LAWSON2B) ? U2 + N : nullptr; // Lawson2b second input
-    double* extra = X + (scheme == MM_ETD2RK ? 3 : (scheme == MM_LAWSON2B ? 4 : 2)) * N;
+    double* extra = X + (scheme == MM_ETD2RK || scheme == MM_EXPEULER_ALT ? 3 : (scheme == MM_LAWSON2B ? 4 : 2)) * N;
     double* Gn = extra;                                     // Riccati
     double* XB = extra + N;
     const PointwiseG pg = pointwise_of(g);
@@ -414,6 +417,22 @@ int run_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, i
             e2.kind = EPI_ETD_S2; e2.alpha = tau * pow(2.0, d - 1); e2.U = U; e2.U2 = U2;
             e2.status = p->status;
             rc = run_tucker(p, 2, W2, other, e2, s);
+            break;
+        }
+        case MM_EXPEULER_ALT: {
+            // Z = U x_mu e^{tau A_mu} (from a copy of U, which the chain consumes), then
+            // U = tau G(U) x_mu phi_1(tau A_mu) + Z in the last epilogue
+            double* Z = U2;
+            MM_CUDA_TRY(cudaMemcpyAsync(X, U, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            Epi e0{};
+            e0.kind = EPI_STORE; e0.alpha = 1.0; e0.C = Z;
+            rc = run_tucker(p, 0, X, Y, e0, s);
+            if (rc) break;
+            rc = launch_prepass(stencil_base(p, U, X, PRE_G, t, pg), s);
+            if (rc) break;
+            Epi e1{};
+            e1.kind = EPI_STORE; e1.alpha = tau; e1.C = U; e1.D1 = Z; e1.beta = 1.0;
+            rc = run_tucker(p, 1, X, Y, e1, s);
             break;
         }
         case MM_EXPROSEULER: {

@@ -39,9 +39,11 @@ ETD2RK = 1      # ETD2RK, eq. (12); tensor form eq. (20)
 LAWSON_EULER = 2  # Lawson-Euler, eq. (9); tensor form eq. (17)
 LAWSON2B = 3    # Lawson2b, eq. (10); tensor form eq. (18)
 EXPROSEULER = 4  # exponential Rosenbrock-Euler, eq. (13); tensor form eq. (21) (Riccati)
+EXPEULER_ALT = 5  # exponential Euler, alternative form (Section 3.2)
 
 SCHEME_NAMES = {EXPEULER: "expeuler", ETD2RK: "etd2rk",
-                LAWSON_EULER: "lawson_euler", LAWSON2B: "lawson2b", EXPROSEULER: "exprosenbrock"}
+                LAWSON_EULER: "lawson_euler", LAWSON2B: "lawson2b", EXPROSEULER: "exprosenbrock",
+                EXPEULER_ALT: "expeuler_alt"}
 
 
 @dataclasses.dataclass
@@ -271,6 +273,9 @@ def workload(name: str, **over) -> Problem:
         "adr3d_n256_etd2rk": lambda: adr_3d(256, 0.5, 1.0, 3, 1e-3, 100, ETD2RK),
         "riccati_n2048_expeuler": lambda: riccati_2d(2048, 5, 1e-4, 50, EXPEULER),
         "riccati_n2048_etd2rk": lambda: riccati_2d(2048, 5, 1e-4, 50, ETD2RK),
+        # the paper's LQ-control problem (Section 4.1), nhat = 30, T = 0.025, 170 steps
+        "lq_riccati_nhat30_etd2rk": lambda: lq_riccati(30, 170, ETD2RK),
+        "lq_riccati_nhat30_exprosenbrock": lambda: lq_riccati(30, 170, EXPROSEULER),
     }
     if name in BATCHED:
         raise ValueError(f"{name} is a batch: use batched_workload()")

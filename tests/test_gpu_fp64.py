@@ -227,3 +227,9 @@ def test_rosenbrock_rejects_other_nonlinearities(api):
     with pytest.raises(api.PhisplitError) as e:
         api.expint_step(plan, wl.EXPROSEULER, U, 1, g=g)
     assert e.value.code == -3
+
+
+def test_expeuler_alternative_form_matches_oracle(api):
+    p = wl.adr_3d(seed=5, steps=4, scheme=wl.EXPEULER_ALT, sizes=(20, 17, 13))
+    got, ref = run_pair(api, p)
+    assert rel_err_inf(got, ref) <= TOL

@@ -94,7 +94,8 @@ def observed_orders(scheme, cubic=(0.0, -0.5, 1.5, -1.0), T=0.5, steps=(8, 16, 3
 
 
 @pytest.mark.parametrize("scheme,order", [(oi.EXPEULER, 1), (oi.ETD2RK, 2),
-                                          (oi.LAWSON_EULER, 1), (oi.LAWSON2B, 2)])
+                                          (oi.LAWSON_EULER, 1), (oi.LAWSON2B, 2),
+                                          (oi.EXPEULER_ALT, 1)])
 def test_observed_order(scheme, order):
     """Global order on a step sweep: 1 for (Lawson-/exponential) Euler, 2 for
     ETD2RK and Lawson2b, as in the paper's order tables (Section 4)."""
@@ -209,3 +210,15 @@ def test_lq_riccati_reaches_the_algebraic_riccati_solution():
         op = OracleProblem.from_problem(p, lmax=2)
         U = integrate(op, p.u0, scheme, steps)
         assert oi.rel_err_fro(U.T, X) < 1e-6, scheme
+
+
+def test_expeuler_alternative_form_exact_for_linear_problems():
+    """The alternative exponential Euler form (Section 3.2) is exact for linear
+    autonomous problems: with g = 0 it is e^{tau K} u, step after step."""
+    ns = (4, 5, 3)
+    As = [wl.fd_matrix(n, 0.3, 0.2) for n in ns]
+    U = wl.random_tensor(tuple(reversed(ns)), 2)
+    op = OracleProblem(A=As, tau=0.07)
+    got = integrate(op, U, oi.EXPEULER_ALT, 3)
+    ref = scipy.linalg.expm(0.21 * kron_sum(As)) @ vec(U)
+    assert np.abs(vec(got) - ref).max() < 1e-12
