@@ -233,3 +233,29 @@ def test_expeuler_alternative_form_matches_oracle(api):
     p = wl.adr_3d(seed=5, steps=4, scheme=wl.EXPEULER_ALT, sizes=(20, 17, 13))
     got, ref = run_pair(api, p)
     assert rel_err_inf(got, ref) <= TOL
+
+
+@pytest.fixture(scope="module")
+def lq_ref():
+    """The paper's LQ problem (nhat = 30) at T = 0.025 from the oracle: Richardson
+    extrapolation of ETD2RK at 170 and 340 steps, plus the printed errors."""
+    from tests.test_oracle_paper import lq_golden, lq_reference
+    ref, _ = lq_reference(30, 170)
+    return ref, {(s, n): e for (_, s, n, e) in lq_golden()}
+
+
+@pytest.mark.parametrize("scheme,prec", [(wl.ETD2RK, "fp64"), (wl.EXPROSEULER, "fp64"),
+                                         (wl.ETD2RK, "bf16x3")])
+def test_lq_riccati_reproduces_printed_errors(api, lq_ref, scheme, prec):
+    """GPU runs of the paper's LQ problem (Section 4.1, nhat = 30) at 30 steps land on
+    the errors printed in Figure "riccati" (ETD2RK 1.7186e-4, exponential
+    Rosenbrock-Euler 1.6105e-4) to 0.5 %; the BF16x3 form adds ~1e-7 to them."""
+    ref, printed = lq_ref
+    p = wl.lq_riccati(30, 30, scheme)
+    plan, g, U = api.setup(p, prec)
+    api.expint_step(plan, scheme, U, 30, g=g)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    e = rel_err_fro(U.cpu().numpy(), ref)
+    key = ("etd2rk" if scheme == wl.ETD2RK else "exprosenbrock", 30)
+    assert abs(e / printed[key] - 1) < 5e-3, (e, printed[key])

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle.integrators as oi
-from oracle.integrators import OracleProblem, integrate, rel_err_inf
+from oracle.integrators import OracleProblem, integrate, rel_err_fro, rel_err_inf
 from paper_2304_02327_gb300 import workloads as wl
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_adr_errors.txt")
@@ -66,3 +66,36 @@ def test_oracle_reproduces_paper_error(sizes, scheme, steps, err):
     # The printed values agree with the oracle to ~1e-11 relative; 1e-8 leaves
     # room for the paper's quadrature-based phi_l and BLAS summation order.
     assert abs(got - err) <= 1e-8 * err, (got, err)
+
+
+def lq_golden():
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_lq_riccati_errors.txt")):
+        if line.strip() and not line.startswith("#"):
+            nhat, scheme, steps, err = line.split()
+            rows.append((int(nhat), scheme, int(steps), float(err)))
+    return rows
+
+
+def lq_reference(nhat, n_coarse):
+    """The LQ solution at T: Richardson extrapolation of the oracle's ETD2RK at
+    n_coarse and 2 n_coarse steps (a second-order method, so (4 U_fine - U_coarse)/3)."""
+    def run(m):
+        p = wl.lq_riccati(nhat, m, wl.ETD2RK)
+        return integrate(OracleProblem.from_problem(p), p.u0, wl.ETD2RK, m)
+    a, b = run(n_coarse), run(2 * n_coarse)
+    return (4 * b - a) / 3, rel_err_fro(b, (4 * b - a) / 3)
+
+
+def test_lq_riccati_printed_error():
+    """The oracle's ETD2RK PHISPLIT on the paper's LQ problem (nhat = 30) reproduces
+    the printed errors (Figure "riccati"): against a reference extrapolated from 170
+    and 340 steps, the 340-step solution's error is a quarter of the printed 170-step
+    error (second order), and the 30-step error is the printed 1.7186e-4 to 0.3 %."""
+    printed = {(s, n): e for (_, s, n, e) in lq_golden()}
+    ref, gap = lq_reference(30, 170)
+    assert abs(gap / (printed[("etd2rk", 170)] / 4) - 1) < 0.05, gap
+    p = wl.lq_riccati(30, 30, wl.ETD2RK)
+    got = integrate(OracleProblem.from_problem(p), p.u0, wl.ETD2RK, 30)
+    e = rel_err_fro(got, ref)
+    assert abs(e / printed[("etd2rk", 30)] - 1) < 3e-3, e
