@@ -68,7 +68,7 @@ __device__ __forceinline__ TileAt tile_at(const BInst* __restrict__ tab, const i
     return TileAt{inst, (lt % tiles1) * kT, (lt / tiles1) * kT};
 }
 
-__global__ void __launch_bounds__(256) batch_prepass_kernel(const BInst* __restrict__ tab,
+__global__ void __launch_bounds__(256, 4) batch_prepass_kernel(const BInst* __restrict__ tab,
                                                             const int64_t* __restrict__ tile_begin, int count,
                                                             int64_t ntiles, float t, int prec) {
     __shared__ float2 sp[kT + 2][kT + 2];
@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(256) batch_prepass_kernel(const BInst* __restr
     };
     TileAt cur = tile_at(tab, tile_begin, inst, T0);
     fetch(cur);
+    const int c = threadIdx.x % kT;
     for (int64_t T = T0; T < T1; ++T) {
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
@@ -108,45 +109,43 @@ __global__ void __launch_bounds__(256) batch_prepass_kernel(const BInst* __restr
                 (&sp[0][0])[e] = v;
             }
         }
-        const BInst b = tab[cur.inst];  // by value: the stores below cannot alias it
+        // this tile's instance data (loaded before the stores below, which cannot
+        // alias them once in registers)
+        const BInst& bi = tab[cur.inst];
+        const int n1 = bi.n1, n2 = bi.n2, p1 = bi.p1;
+        const float* cf1 = bi.coef1;
+        const float* cf2 = bi.coef2;
+        uint8_t* wbase = bi.wbase;
+        const int64_t wpp = bi.w_part_pitch, woff = bi.w_off;
+        const PointwiseG g = bi.g;
         const int a1 = cur.a1, a2 = cur.a2;
         if (T + 1 < T1) {                // the next tile's loads overlap this tile's stencil
             while (T + 1 >= next) next = __ldg(tile_begin + (++inst) + 1);
             cur = tile_at(tab, tile_begin, inst, T + 1);
             fetch(cur);
         }
-        __syncthreads();
-        const int n1 = b.n1, n2 = b.n2;
-        const int c = threadIdx.x % kT;
+        // coefficients along i_1 are fixed for this thread's column of the tile
         const int i1 = a1 + c;
+        const bool in1 = i1 < n1;
+        const float c1a = in1 ? __ldg(cf1 + i1) : 0.f, c1c = in1 ? __ldg(cf1 + n1 + i1) : 0.f,
+                    c1s = in1 ? __ldg(cf1 + 2 * n1 + i1) : 0.f;
+        __syncthreads();
 #pragma unroll
         for (int q = 0; q < kT / 8; ++q) {
             const int r = threadIdx.x / kT + 8 * q;
             const int i2 = a2 + r;
-            if (i1 >= n1 || i2 >= n2) continue;
+            if (!in1 || i2 >= n2) continue;
             const float uh = sp[r + 1][c + 1].x, ul = sp[r + 1][c + 1].y;
             const float u = uh + ul;
-            const int i = i1 + n1 * i2;
-            float acc = mx::g32(b.g, u, t, i);
-            acc = fmaf(b.coef1[2 * n1 + i1], u, acc);
-            if (i1 > 0) {
-                const float2 v = sp[r + 1][c];
-                acc = fmaf(b.coef1[i1], (v.x - uh) + (v.y - ul), acc);
-            }
-            if (i1 + 1 < n1) {
-                const float2 v = sp[r + 1][c + 2];
-                acc = fmaf(b.coef1[n1 + i1], (v.x - uh) + (v.y - ul), acc);
-            }
-            acc = fmaf(b.coef2[2 * n2 + i2], u, acc);
-            if (i2 > 0) {
-                const float2 v = sp[r][c + 1];
-                acc = fmaf(b.coef2[i2], (v.x - uh) + (v.y - ul), acc);
-            }
-            if (i2 + 1 < n2) {
-                const float2 v = sp[r + 2][c + 1];
-                acc = fmaf(b.coef2[n2 + i2], (v.x - uh) + (v.y - ul), acc);
-            }
-            store_parts_prec(prec, b.wbase, b.w_part_pitch, b.w_off + i1 + (int64_t)b.p1 * i2, acc, 0.f);
+            float acc = mx::g32(g, u, t, i1 + n1 * i2);
+            // the edge coefficients are exactly zero and the halo holds zeros there
+            acc = fmaf(c1s, u, acc);
+            acc = fmaf(c1a, (sp[r + 1][c].x - uh) + (sp[r + 1][c].y - ul), acc);
+            acc = fmaf(c1c, (sp[r + 1][c + 2].x - uh) + (sp[r + 1][c + 2].y - ul), acc);
+            acc = fmaf(__ldg(cf2 + 2 * n2 + i2), u, acc);
+            acc = fmaf(__ldg(cf2 + i2), (sp[r][c + 1].x - uh) + (sp[r][c + 1].y - ul), acc);
+            acc = fmaf(__ldg(cf2 + n2 + i2), (sp[r + 2][c + 1].x - uh) + (sp[r + 2][c + 1].y - ul), acc);
+            store_parts_prec(prec, wbase, wpp, woff + i1 + (int64_t)p1 * i2, acc, 0.f);
         }
         __syncthreads();
     }
