@@ -514,7 +514,7 @@ def ours(args):
         achieved = tflops / (k_ms / n_launch / 1e3) / 1e12 if n_launch else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": profile_traffic("contract_tf32", args.workload),
+                "traffic": profile_traffic(f"contract_{args.prec}", args.workload),
                 "kernel": "tf32x3_mode_kernel (tcgen05 mu-mode contraction)",
                 "launches": n_launch, "avg_launch_ms": k_ms / n_launch if n_launch else None,
                 "share_of_step_time": (k_ms / ksteps) / (t_ms / args.steps) if t_ms else None,

@@ -360,6 +360,7 @@ extern "C" int mm_batch_tile_plan(int count, const int64_t* n1, const int64_t* n
 
 extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plans, const mm_nonlin* g,
                                    double* const* U, int scheme, const mm_tune* tune, void* stream) {
+    NvtxScope nv("expint_batch_create");
     if (!out) return MM_ERR_ARG;
     *out = nullptr;
     if (count < 1 || !plans || !U) return MM_ERR_ARG;
@@ -543,6 +544,7 @@ fail:
 // The nonlinearities of a batch are autonomous (g = 0 or a cubic in u), so t0 only
 // documents the caller's clock.
 extern "C" int expint_batch_run(mm_batch b, double t0, int nsteps, void* stream) {
+    NvtxScope nv("expint_batch_run");
     if (!b || nsteps < 0 || !isfinite(t0)) return MM_ERR_ARG;
     if (nsteps == 0) return MM_OK;
     cudaStream_t s = (cudaStream_t)stream;

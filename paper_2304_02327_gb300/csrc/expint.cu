@@ -273,6 +273,7 @@ extern "C" size_t mumode_workspace_bytes(mm_plan p) {
 
 extern "C" int mumode_phi_apply(mm_plan p, int ell, const double* V, double* P, double alpha,
                                 void* ws, size_t ws_bytes, void* stream) {
+    NvtxScope nv("mumode_phi_apply");
     if (!p || !V || !P || ell < 0 || ell > p->ell_max || !isfinite(alpha)) return MM_ERR_ARG;
     const size_t bytes = (size_t)p->N * sizeof(double);
     if (overlaps(V, bytes, P, bytes)) return MM_ERR_ARG;
@@ -320,6 +321,7 @@ extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin*
 
 extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,
                            int nsteps, void* ws, size_t ws_bytes, void* stream) {
+    NvtxScope nv("expint_step");
     if (!p || !U || nsteps < 0 || !isfinite(t0)) return MM_ERR_ARG;
     const int ell = scheme_ell(scheme);
     if (ell < 0) return MM_ERR_ARG;

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "plan.cuh"
+#include "trace.cuh"
 
 namespace mm {
 
@@ -207,6 +208,7 @@ using namespace mm;
 
 extern "C" int phi_plan_create(mm_plan* out, int d, const int64_t* n, const double* const* A,
                                double tau, int ell_max, int prec, void* stream) {
+    NvtxScope nv("phi_plan_create");
     if (!out) return MM_ERR_ARG;
     *out = nullptr;
     if (!n || !A || d < 1 || d > MM_MAX_D || ell_max < 0 || ell_max > 3 || !isfinite(tau))

@@ -2,6 +2,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "trace.cuh"
 
 namespace mm {
@@ -20,6 +22,9 @@ size_t g_used = 0;
 
 thread_local bool t_capturing = false;
 thread_local long long t_cap[KC_COUNT] = {};
+
+NvtxScope::NvtxScope(const char* name) { nvtxRangePushA(name); }
+NvtxScope::~NvtxScope() { nvtxRangePop(); }
 
 void trace_count(int cls, long long n) {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -26,6 +26,14 @@ void trace_capture_end(long long* counts);
 // True while launches are being timed with events (graph replay would hide them).
 bool trace_timing_on();
 
+// RAII NVTX range around a library entry point (visible in Nsight timelines; costs
+// nothing without a profiler attached).
+class NvtxScope {
+public:
+    explicit NvtxScope(const char* name);
+    ~NvtxScope();
+};
+
 class TraceScope {
 public:
     TraceScope(int cls, cudaStream_t s);

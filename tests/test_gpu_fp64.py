@@ -259,3 +259,19 @@ def test_lq_riccati_reproduces_printed_errors(api, lq_ref, scheme, prec):
     e = rel_err_fro(U.cpu().numpy(), ref)
     key = ("etd2rk" if scheme == wl.ETD2RK else "exprosenbrock", 30)
     assert abs(e / printed[key] - 1) < 5e-3, (e, printed[key])
+
+
+
+def test_checkpoint_resume_is_bit_identical_fp64(api):
+    p = wl.paper_adr_3d((20, 21, 22), steps=6, scheme=wl.ETD2RK)
+    plan, g, U = api.setup(p, "fp64")
+    api.expint_step(plan, p.scheme, U, 6, g=g)
+    plan2, g2, V = api.setup(p, "fp64")
+    api.expint_step(plan2, p.scheme, V, 4, g=g2)
+    saved = V.cpu().numpy().copy()
+    plan2.close()
+    plan3, g3, W = api.setup(p, "fp64")
+    W.copy_(torch.from_numpy(saved))
+    api.expint_step(plan3, p.scheme, W, 2, t0=4 * p.tau, g=g3)   # time-dependent g
+    torch.cuda.synchronize()
+    assert torch.equal(U, W)

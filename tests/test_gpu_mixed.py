@@ -55,7 +55,8 @@ def dev(x):
 
 
 @pytest.mark.parametrize("ns", [(64,), (128, 128), (33, 17), (48, 64, 80), (320, 40, 2),
-                                (20, 17, 13), (5, 4, 3, 6), (128, 300), (1, 9, 4)])
+                                (20, 17, 13), (5, 4, 3, 6), (128, 300), (1, 9, 4), (127, 3),
+                                (3, 127, 1)])
 @pytest.mark.parametrize("ell", [0, 1, 2])
 def test_mixed_mumode_apply_matches_oracle(api, form, ns, ell):
     tau = 2e-3
@@ -238,3 +239,23 @@ def test_graph_replay_equals_direct_launches(api, form):
     api.expint_step(plan2, p.scheme, V, 4, g=g2)
     torch.cuda.synchronize()
     assert torch.equal(U, V) and torch.equal(U2, V)
+
+
+
+def test_checkpoint_resume_is_bit_identical(api, form):
+    """A one-step method's state is (U_n, t_n): saving U after 3 of 6 steps, destroying
+    the plan, rebuilding it from (A_mu, tau) and continuing gives exactly the
+    uninterrupted run."""
+    p = wl.adr_3d(seed=5, steps=6, scheme=wl.ETD2RK, sizes=(40, 33, 24))
+    plan, g, U = api.setup(p, form)
+    api.expint_step(plan, p.scheme, U, 6, g=g)
+    plan2, g2, V = api.setup(p, form)
+    api.expint_step(plan2, p.scheme, V, 3, g=g2)
+    saved = V.cpu().numpy().copy()
+    plan2.close()
+    del V
+    plan3, g3, W = api.setup(p, form)
+    W.copy_(torch.from_numpy(saved))
+    api.expint_step(plan3, p.scheme, W, 3, t0=3 * p.tau, g=g3)
+    torch.cuda.synchronize()
+    assert torch.equal(U, W)
