@@ -34,8 +34,11 @@
  *   three, 4 products; BF16x3: both in three BF16 parts, 6 products); the phi
  *   matrices are formed in FP64 and the state update u + tau*y is FP64, while
  *   K u + g and the Tucker intermediates are FP32.  The tensor cores' FP32
- *   accumulation truncates toward zero, which leaves a one-sided relative error of
- *   order 1e-7 * n/128 per Tucker apply (BF16x3 about half of TF32x3).
+ *   accumulation truncates toward zero; the main product of every two K-blocks
+ *   therefore goes to a fresh accumulator that is summed in FP32 registers (round
+ *   to nearest), which keeps the integrations within 1e-6 of the FP64 oracle.
+ *   Dense (non-tridiagonal) A_mu: d = 2 only in the mixed forms, the band of A_mu
+ *   as an FP32 stencil and the remainder on the tensor cores.
  */
 #ifndef PHISPLIT_H
 #define PHISPLIT_H
@@ -117,7 +120,9 @@ typedef struct mm_plan_s* mm_plan;
  *           Read during the call only.
  *   tau     time step (finite).  tau = 0 is allowed (phi_l = I / l!).
  *   ell_max highest phi index needed, 0..3 (ETD2RK needs 2).
- *   prec    MM_FP64 or MM_TF32X3.
+ *   prec    MM_FP64, MM_TF32X3 or MM_BF16X3 (the mixed forms also split the phi
+ *           matrices into their operand parts, and the remainders A_mu - band for
+ *           dense A_mu when d = 2).
  *   stream  ordering stream for the set-up kernels.
  * Synchronises `stream` (it reads norms and band widths back).  Allocates the
  * plan's device memory with cudaMalloc.  Errors: MM_ERR_ARG, MM_ERR_SHAPE,
