@@ -212,9 +212,11 @@ MM_API size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin* g);
  * Graphs: unless turned off (phi_plan_set_graphs), the first call with a given
  * (scheme, g's contents, U, ws, nsteps[, t0 for a time-dependent g]) captures the
  * nsteps steps into a CUDA graph on a stream of the plan, and every call with the
- * same arguments replays it on `stream` (one launch of host work).  The plan keeps
- * the eight most recent graphs.  Calls made while `stream` is being captured, or
- * while event tracing is on (mm_trace_enable(1)), launch the kernels directly.
+ * same arguments replays it on `stream` (one launch of host work).  A graph holds
+ * at most 32 steps: longer calls replay a 32-step graph (and one for the rest), or
+ * launch directly when g depends on t.  The plan keeps the eight most recent
+ * graphs.  Calls made while `stream` is being captured, or while event tracing is
+ * on (mm_trace_enable(1)), launch the kernels directly.
  * Errors: MM_ERR_ARG, MM_ERR_UNSUPPORTED, MM_ERR_WORKSPACE, MM_ERR_CUDA.
  */
 MM_API int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0,

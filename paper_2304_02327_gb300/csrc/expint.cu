@@ -13,6 +13,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "plan.cuh"
 #include "stencil.cuh"
 #include "tf32.cuh"
@@ -201,6 +203,8 @@ namespace {
 int run_steps(mm_plan p, int scheme, const mm_nonlin* g, double* U, double t0, int nsteps, void* ws,
               cudaStream_t s);
 
+constexpr int kGraphSteps = 32;     // most steps one captured graph holds
+
 bool same_nonlin(const mm_nonlin* a, int has_a, const mm_nonlin& b, int has_b) {
     if (has_a != has_b) return false;
     if (!has_a) return true;
@@ -349,14 +353,22 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return run_steps(p, scheme, g, U, t0, nsteps, ws, s);      // the caller is capturing
-    const mm_graph_cache* e = find_graph(p, scheme, g, U, t0, nsteps, ws);
-    if (!e) {
-        int rc = capture_steps(p, scheme, g, U, t0, nsteps, ws);
-        if (rc) return rc;
-        e = &p->graphs.back();
+    // Graphs hold at most kGraphSteps steps: longer calls replay that chunk (g without
+    // time dependence) or launch directly (a time-dependent g bakes t into the nodes).
+    const bool tdep = g && g->kind == MM_G_ADR_MANUFACTURED;
+    if (nsteps > kGraphSteps && tdep) return run_steps(p, scheme, g, U, t0, nsteps, ws, s);
+    for (int done = 0; done < nsteps;) {
+        const int k = std::min(kGraphSteps, nsteps - done);
+        const mm_graph_cache* e = find_graph(p, scheme, g, U, t0, k, ws);
+        if (!e) {
+            int rc = capture_steps(p, scheme, g, U, t0, k, ws);
+            if (rc) return rc;
+            e = &p->graphs.back();
+        }
+        MM_CUDA_TRY(cudaGraphLaunch(e->exec, s));
+        for (int c = 0; c < MM_KC_COUNT; ++c) trace_count(c, e->launches[c]);
+        done += k;
     }
-    MM_CUDA_TRY(cudaGraphLaunch(e->exec, s));
-    for (int c = 0; c < MM_KC_COUNT; ++c) trace_count(c, e->launches[c]);
     return MM_OK;
 }
 

@@ -143,14 +143,21 @@ def test_adr3d_n320_two_steps(api):
     assert rel_err_inf(got, ref) <= TOL
 
 
-@pytest.mark.parametrize("scheme,steps,err", [
-    ("etd2rk", 40, 0.0003034138277914), ("expeuler", 50, 0.0107081236857995),
-    ("lawson_euler", 800, 0.0117169705391758), ("etd2rk", 140, 2.19309513095735e-05)])
-def test_gpu_reproduces_paper_errors(api, scheme, steps, err):
-    """The paper's own 3D ADR test (Section 4.2) on 40x41x42: the CUDA path gives
-    the relative error the paper prints (tests/golden/paper_adr_errors.txt)."""
-    sch = {"etd2rk": wl.ETD2RK, "expeuler": wl.EXPEULER, "lawson_euler": wl.LAWSON_EULER}[scheme]
-    p = wl.paper_adr_3d((40, 41, 42), steps, sch)
+def _paper_rows():
+    from tests.test_oracle_paper import load_golden
+    return [pytest.param(sizes, s, k, e, id=f"{'x'.join(map(str, sizes))}-{s}-{k}")
+            for sizes, s, k, e in load_golden()]
+
+
+@pytest.mark.parametrize("sizes,scheme,steps,err", _paper_rows())
+def test_gpu_reproduces_paper_errors(api, sizes, scheme, steps, err):
+    """The paper's own 3D ADR test (Section 4.2), every printed point (40x41x42 and
+    80x81x82, exponential Euler, ETD2RK, Lawson-Euler, Lawson2b, up to 32800 steps):
+    the CUDA path gives the relative error the paper prints
+    (tests/golden/paper_adr_errors.txt) to 1e-8 of its value."""
+    sch = {"etd2rk": wl.ETD2RK, "expeuler": wl.EXPEULER, "lawson_euler": wl.LAWSON_EULER,
+           "lawson2b": wl.LAWSON2B}[scheme]
+    p = wl.paper_adr_3d(sizes, steps, sch)
     plan, g, U = api.setup(p)
     api.expint_step(plan, sch, U, steps, g=g)
     e = rel_err_inf(U.cpu().numpy(), math.e * p.u0)
