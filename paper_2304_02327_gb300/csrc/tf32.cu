@@ -19,27 +19,33 @@
 //           a0 b0 | a1 b0 + a0 b1 + a2 b0 + a1 b1 + a0 b2
 // The tensor cores' FP32 accumulation truncates toward zero, which biases long
 // sums (measured: a one-sided relative error growing with K).  So the main
-// product of each K-block goes into a fresh TMEM slot (only its four MMAs
-// accumulate in hardware) and the epilogue warps add the slots into FP32 registers
-// with round-to-nearest; the much smaller corrections accumulate in TMEM over the
-// whole tile.  The three-way split of the fixed matrix keeps its rounding, which
-// would repeat identically every step, at 2^-33.
+// product of every kGroup = 2 K-blocks goes into a fresh TMEM slot (only its eight
+// MMAs accumulate in hardware) and the epilogue warps add the slots into FP32
+// registers with round-to-nearest; the much smaller corrections accumulate in TMEM
+// over the whole tile, in an accumulator of their own: added onto the main product,
+// their low-order bits would force a truncation at main-product magnitude into sums
+// that are otherwise exact (an exactly representable operand, such as the 0/alpha
+// matrix B of the LQ Riccati problem, makes every main-product sum exact), and the
+// resulting bias accumulated over the steps of that problem to 1.4e-6 in 30 steps
+// against 1.5e-7 this way.  The three-way split of the fixed matrix keeps its
+// rounding, which would repeat identically every step, at ~2^-25 (BF16) or 2^-33
+// (TF32) of its entries.
 //
 // Kernel structure: persistent, one CTA per SM over tiles t = blockIdx.x + i grid.
-//   warp 0      loader: per K-block, one TMA tensor load per operand part (the
-//               3-D map {K, rows, part} zero-fills the ragged K tail and the last
-//               rows) and bulk copies of this tile's columns of the plan's Phi image
-//   warp 1      MMA issuer (one thread): per K-block the main product into slot
-//               (K-block mod 2) of a two-slot ring, corrections into the tile's
-//               accumulator (two, alternating between tiles)
+//   warp 0      loader: per K-block, one TMA tensor load per part of either
+//               operand (the 3-D maps {K, rows, part} zero-fill the ragged K tail
+//               and the last rows)
+//   warp 1      MMA issuer (one thread): per K-block one asm block of main-product
+//               MMAs into the current slot of a two-slot ring (a fresh slot every
+//               kGroup K-blocks) and one of corrections into the tile's accumulator
 //   warps 2-17  epilogue, four warps per TMEM lane quarter, each owning a quarter
 //               of the columns: drain each main slot into register accumulators as
-//               it completes (all chunk loads issued before one wait), then add the
-//               corrections and write the next mode's split operand (or FP32 after
-//               the last mode); the two-slot ring lets the MMAs of the next tile's
-//               first K-blocks run meanwhile
-// TMEM: [main slot 0 | main slot 1 | corr tile-even | corr tile-odd], nc each.
-// Every mbarrier wait is bounded (tcgen05.cuh).
+//               it completes, then add the corrections and write the next mode's
+//               split operand (or FP32 after the last mode); the two-slot ring lets
+//               the MMAs of the next tile's first K-blocks run meanwhile
+// TMEM: [main slot 0 | main slot 1 | corrections], nc columns each; the next tile's
+// corrections wait until the epilogue has read this tile's.  Every mbarrier wait is
+// bounded (tcgen05.cuh).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -78,13 +84,114 @@ template <class F> __device__ __forceinline__ uint32_t idesc_of(int nc);
 template <> __device__ __forceinline__ uint32_t idesc_of<FormTF32>(int nc) { return tc::idesc_tf32(128, nc); }
 template <> __device__ __forceinline__ uint32_t idesc_of<FormBF16>(int nc) { return tc::idesc_bf16(128, nc); }
 
-template <class F> __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc);
-template <> __device__ __forceinline__ void mma<FormTF32>(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    tc::mma_tf32(d, a, b, id, acc);
+// ---- the MMAs of one K-block, each group from a single asm block ----------
+// One thread issues every MMA of the CTA, so its instruction count per MMA bounds
+// the tensor pipe: at ~90 cycles per MMA (per-MMA descriptor arithmetic and
+// predicate set-up) it, not the pipe (N / 2 cycles at N = 160), set the tile time.
+// Here a descriptor is assembled from two 32-bit words: the low word is the start
+// address field (shared-memory address / 16, < 2^14 so an offset never carries out
+// of it) plus the LBO bit, the high word (stride 1024 B, version, 128-byte swizzle)
+// is the same for every operand.  A part tile q starts 16 KB (1024 units) after part
+// 0, B part q at q * bstep units, and K slice kk at 2 kk units (32 bytes).
+constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint32_t desc_lo(uint32_t addr) { return ((addr & 0x3FFFFu) >> 4) | (1u << 16); }
+
+#define MM_TC_MMA(KIND, D, AOFF, B, BOFF, P)                         \
+    "add.u32 la, %1, " AOFF ";\n\t"                                 \
+    "add.u32 lb, " B ", " BOFF ";\n\t"                              \
+    "mov.b64 da, {la, %3};\n\t"                                     \
+    "mov.b64 db, {lb, %3};\n\t"                                     \
+    "tcgen05.mma.cta_group::1.kind::" KIND " [" D "], da, db, %4, " P ";\n\t"
+
+// main product a0 b0 over the four K slices; the first one overwrites unless acc
+#define MM_TC_MAIN(KIND)                                                                 \
+    asm volatile(                                                                        \
+        "{\n\t.reg .pred pa, pt;\n\t.reg .b32 la, lb;\n\t.reg .b64 da, db;\n\t"       \
+        "setp.ne.b32 pa, %5, 0;\n\t"                                                    \
+        "setp.eq.b32 pt, %5, %5;\n\t"                                                   \
+        MM_TC_MMA(KIND, "%0", "0", "%2", "0", "pa")                                      \
+        MM_TC_MMA(KIND, "%0", "2", "%2", "2", "pt")                                      \
+        MM_TC_MMA(KIND, "%0", "4", "%2", "4", "pt")                                      \
+        MM_TC_MMA(KIND, "%0", "6", "%2", "6", "pt")                                      \
+        "}" ::"r"(d), "r"(alo), "r"(blo), "r"(kDescHi), "r"(idesc), "r"(acc)              \
+        : "memory")
+
+template <class F>
+__device__ __forceinline__ void mma_main(uint32_t d, uint32_t alo, uint32_t blo, uint32_t idesc, uint32_t acc);
+template <>
+__device__ __forceinline__ void mma_main<FormTF32>(uint32_t d, uint32_t alo, uint32_t blo, uint32_t idesc,
+                                                   uint32_t acc) {
+    MM_TC_MAIN("tf32");
 }
-template <> __device__ __forceinline__ void mma<FormBF16>(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    tc::mma_bf16(d, a, b, id, acc);
+template <>
+__device__ __forceinline__ void mma_main<FormBF16>(uint32_t d, uint32_t alo, uint32_t blo, uint32_t idesc,
+                                                   uint32_t acc) {
+    MM_TC_MAIN("f16");
 }
+
+// corrections of one K block (slice-major, the form's pairs within a slice) into d;
+// the first overwrites unless acc.  b1, b2: B parts 1 and 2.
+#define MM_TC_CORR_PRE                                                                   \
+    "{\n\t.reg .pred pa, pt;\n\t.reg .b32 la, lb, b1, b2;\n\t.reg .b64 da, db;\n\t"   \
+    "setp.ne.b32 pa, %5, 0;\n\t"                                                        \
+    "setp.eq.b32 pt, %5, %5;\n\t"                                                       \
+    "add.u32 b1, %2, %6;\n\t"                                                           \
+    "add.u32 b2, b1, %6;\n\t"
+
+template <class F>
+__device__ __forceinline__ void mma_corr(uint32_t d, uint32_t alo, uint32_t blo, uint32_t bstep, uint32_t idesc,
+                                         uint32_t acc);
+// TF32x3: a1 b0, a0 b1, a0 b2 per slice
+template <>
+__device__ __forceinline__ void mma_corr<FormTF32>(uint32_t d, uint32_t alo, uint32_t blo, uint32_t bstep,
+                                                   uint32_t idesc, uint32_t acc) {
+    asm volatile(MM_TC_CORR_PRE
+                 MM_TC_MMA("tf32", "%0", "1024", "%2", "0", "pa")
+                 MM_TC_MMA("tf32", "%0", "0", "b1", "0", "pt")
+                 MM_TC_MMA("tf32", "%0", "0", "b2", "0", "pt")
+                 MM_TC_MMA("tf32", "%0", "1026", "%2", "2", "pt")
+                 MM_TC_MMA("tf32", "%0", "2", "b1", "2", "pt")
+                 MM_TC_MMA("tf32", "%0", "2", "b2", "2", "pt")
+                 MM_TC_MMA("tf32", "%0", "1028", "%2", "4", "pt")
+                 MM_TC_MMA("tf32", "%0", "4", "b1", "4", "pt")
+                 MM_TC_MMA("tf32", "%0", "4", "b2", "4", "pt")
+                 MM_TC_MMA("tf32", "%0", "1030", "%2", "6", "pt")
+                 MM_TC_MMA("tf32", "%0", "6", "b1", "6", "pt")
+                 MM_TC_MMA("tf32", "%0", "6", "b2", "6", "pt")
+                 "}" ::"r"(d), "r"(alo), "r"(blo), "r"(kDescHi), "r"(idesc), "r"(acc), "r"(bstep)
+                 : "memory");
+}
+// BF16x3: a1 b0, a0 b1, a2 b0, a1 b1, a0 b2 per slice
+template <>
+__device__ __forceinline__ void mma_corr<FormBF16>(uint32_t d, uint32_t alo, uint32_t blo, uint32_t bstep,
+                                                   uint32_t idesc, uint32_t acc) {
+    asm volatile(MM_TC_CORR_PRE
+                 MM_TC_MMA("f16", "%0", "1024", "%2", "0", "pa")
+                 MM_TC_MMA("f16", "%0", "0", "b1", "0", "pt")
+                 MM_TC_MMA("f16", "%0", "2048", "%2", "0", "pt")
+                 MM_TC_MMA("f16", "%0", "1024", "b1", "0", "pt")
+                 MM_TC_MMA("f16", "%0", "0", "b2", "0", "pt")
+                 MM_TC_MMA("f16", "%0", "1026", "%2", "2", "pt")
+                 MM_TC_MMA("f16", "%0", "2", "b1", "2", "pt")
+                 MM_TC_MMA("f16", "%0", "2050", "%2", "2", "pt")
+                 MM_TC_MMA("f16", "%0", "1026", "b1", "2", "pt")
+                 MM_TC_MMA("f16", "%0", "2", "b2", "2", "pt")
+                 MM_TC_MMA("f16", "%0", "1028", "%2", "4", "pt")
+                 MM_TC_MMA("f16", "%0", "4", "b1", "4", "pt")
+                 MM_TC_MMA("f16", "%0", "2052", "%2", "4", "pt")
+                 MM_TC_MMA("f16", "%0", "1028", "b1", "4", "pt")
+                 MM_TC_MMA("f16", "%0", "4", "b2", "4", "pt")
+                 MM_TC_MMA("f16", "%0", "1030", "%2", "6", "pt")
+                 MM_TC_MMA("f16", "%0", "6", "b1", "6", "pt")
+                 MM_TC_MMA("f16", "%0", "2054", "%2", "6", "pt")
+                 MM_TC_MMA("f16", "%0", "1030", "b1", "6", "pt")
+                 MM_TC_MMA("f16", "%0", "6", "b2", "6", "pt")
+                 "}" ::"r"(d), "r"(alo), "r"(blo), "r"(kDescHi), "r"(idesc), "r"(acc), "r"(bstep)
+                 : "memory");
+}
+#undef MM_TC_CORR_PRE
+#undef MM_TC_MAIN
+#undef MM_TC_MMA
 
 // One class of tiles: instances of equal shape whose operands sit packed one after
 // the other (instance j's tensor operand rows at j * rows, its matrix operand rows
@@ -122,6 +229,10 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"(map), "r"(k0), "r"(row0), "r"(part), "r"(bar)
         : "memory");
 }
+
+template <int E> struct PartType;
+template <> struct PartType<2> { using type = uint16_t; };
+template <> struct PartType<4> { using type = uint32_t; };
 
 struct TileId {
     int c, inst, rt, sp;
@@ -194,6 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             int64_t issued_last[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) issued_last[s] = -1;
             int64_t it = 0;
+            int s = 0;                     // it mod stages
+            uint32_t ph = 0;               // (it / stages) mod 2
             bool ok = true;
             for (int64_t i = 0; i < my_tiles && ok; ++i) {
                 const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
@@ -202,8 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                 const int col0 = id.inst * k.ncols + id.sp * k.nc;
                 const uint32_t b_tile = (uint32_t)k.nc * kRowBytes;
                 for (int kb = 0; kb < k.nkb; ++kb, ++it) {
-                    const int s = (int)(it % stages);
-                    if (it >= stages && !tc::mbar_wait(empty(s), (uint32_t)((it / stages) - 1) & 1, g.status)) {
+                    if (it >= stages && !tc::mbar_wait(empty(s), ph ^ 1u, g.status)) {
                         ok = false;
                         break;
                     }
@@ -214,6 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                     for (int part = 0; part < kBParts; ++part)   // rows col0.. of b0, b1, b2
                         tma_load_3d(st + a_bytes + part * b_slot, &k.mmap, kb * F::kBK, col0, part, full(s));
                     issued_last[s] = it;
+                    if (++s == stages) { s = 0; ph ^= 1u; }
                 }
             }
             // never leave the CTA with copies in flight
@@ -224,11 +337,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            int64_t it = 0;                // stages issued
+            int s = 0;                     // stage of the next K-block
+            uint32_t ph = 0;               // its fill phase parity
             int64_t git = 0;               // main-slot groups issued
             int64_t uses[2] = {0, 0};      // uses of each main slot so far
             bool ok = true;
             const uint32_t corr = tmem + (uint32_t)(2 * g.stage_nc);   // the tile's corrections
+            const uint32_t sbase = tc::smem_u32(smem);
+            const uint32_t bstep = b_slot >> 4;                        // one B part, descriptor units
             for (int64_t i = 0; i < my_tiles && ok; ++i) {
                 const TileId id = tile_of(g, blockIdx.x + i * gridDim.x);
                 const TcClass& k = g.cls[id.c];
@@ -238,8 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                 // tile, free again once the epilogue has read the previous tile's (its
                 // wait comes after the first stage's main products are queued)
                 int r = 0;
-                for (int kb = 0; kb < k.nkb; ++kb, ++it) {
-                    const int s = (int)(it % stages);
+                for (int kb = 0; kb < k.nkb; ++kb) {
                     const bool gfirst = (kb % kGroup) == 0;
                     const bool glast = (kb % kGroup) == kGroup - 1 || kb == k.nkb - 1;
                     if (gfirst) {
@@ -250,33 +365,22 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                         }
                         ++uses[r];
                     }
-                    if (!tc::mbar_wait(full(s), (uint32_t)(it / stages) & 1, g.status)) { ok = false; break; }
+                    if (!tc::mbar_wait(full(s), ph, g.status)) { ok = false; break; }
                     tc::tc_fence_after();
-                    const uint32_t mainacc = tmem + (uint32_t)(r * g.stage_nc);
-                    const uint32_t abase = tc::smem_u32(smem + s * stage_bytes);
-                    // descriptors of the stage's tiles; an offset of o bytes adds o / 16
-                    const uint64_t da = tc::desc_k_sw128(abase);
-                    const uint64_t db = tc::desc_k_sw128(abase + a_bytes);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        mma<F>(mainacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idd,
-                               (kk != 0 || !gfirst) ? 1u : 0u);
+                    const uint32_t abase = sbase + (uint32_t)s * stage_bytes;
+                    const uint32_t alo = desc_lo(abase), blo = desc_lo(abase + a_bytes);
+                    mma_main<F>(tmem + (uint32_t)(r * g.stage_nc), alo, blo, idd, gfirst ? 0u : 1u);
                     if (kb == 0 && i >= 1 && !tc::mbar_wait(cempty(0), (uint32_t)((i - 1) & 1), g.status)) {
                         ok = false;
                         break;
                     }
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-                        for (int c = 0; c < F::kCorr; ++c)
-                            mma<F>(corr, da + (uint64_t)((F::corr_a(c) * kATile + kk * 32) >> 4),
-                                   db + (uint64_t)((F::corr_b(c) * b_slot + kk * 32) >> 4), idd,
-                                   (c == 0 && (kb | kk) == 0) ? 0u : 1u);
+                    mma_corr<F>(corr, alo, blo, bstep, idd, kb == 0 ? 0u : 1u);
                     tc::mma_commit(empty(s));
                     if (glast) {
                         tc::mma_commit(mfull(r));
                         ++git;
                     }
+                    if (++s == stages) { s = 0; ph ^= 1u; }
                 }
                 if (ok) tc::mma_commit(cfull(0));
             }
@@ -350,22 +454,46 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             // output column col of row q: next-mode position jq + p' (rq + (R / n') col)
             // (or q + ldy col for FP32); successive columns step by dpos
             const int64_t dpos = k.last ? k.ldy : (int64_t)k.next_p * k.next_rows_per_i;
-            float* yb = k.last ? k.yout + (int64_t)id.inst * k.y_stride : nullptr;
-            const int64_t pbase = k.last ? 0 : (int64_t)id.inst * k.p_stride;
+            if (k.last) {
+                float* const yb = k.yout + (int64_t)id.inst * k.y_stride + q;
+                const bool accum = k.accum != 0;
 #pragma unroll
-            for (int c = 0; c < kQuartCols / 16; ++c) {
-                if (c0 + c >= c1) continue;
-                const int i0 = col0 + (c0 + c) * 16;
-                int64_t pos = k.last ? q + k.ldy * (int64_t)i0
-                                     : pbase + jq + (int64_t)k.next_p * (rq + k.next_rows_per_i * (int64_t)i0);
-                const int lim = min(16, k.ncols - i0);
+                for (int c = 0; c < kChunks; ++c) {
+                    if (c0 + c >= c1) continue;
+                    const int i0 = col0 + (c0 + c) * 16;
+                    float* y = yb + k.ldy * (int64_t)i0;
+                    const int lim = min(16, k.ncols - i0);
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    if (u >= lim) break;
-                    const float y = acc[c * 16 + u];
-                    if (k.last) yb[pos] = k.accum ? yb[pos] + y : y;
-                    else store_parts<F>(k.pout, k.out_part_pitch, pos, y, 0.f);
-                    pos += dpos;
+                    for (int u = 0; u < 16; ++u) {
+                        if (u >= lim) break;
+                        *y = accum ? *y + acc[c * 16 + u] : acc[c * 16 + u];
+                        y += dpos;
+                    }
+                }
+            } else {
+                // the parts of one element sit part_pitch apart; three pointers walk
+                // the columns together
+                using T = typename PartType<F::kElem>::type;
+                const int64_t pp = k.out_part_pitch;
+                T* const ob = (T*)k.pout + (int64_t)id.inst * k.p_stride + jq;
+#pragma unroll
+                for (int c = 0; c < kChunks; ++c) {
+                    if (c0 + c >= c1) continue;
+                    const int i0 = col0 + (c0 + c) * 16;
+                    T* p0 = ob + (int64_t)k.next_p * (rq + k.next_rows_per_i * (int64_t)i0);
+                    T* p1 = p0 + pp;
+                    T* p2 = F::kAParts == 3 ? p1 + pp : p1;
+                    const int lim = min(16, k.ncols - i0);
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        if (lim < 16 && u >= lim) break;
+                        uint32_t v[3];
+                        split_parts<F>(acc[c * 16 + u], 0.f, v);
+                        *p0 = (T)v[0];
+                        *p1 = (T)v[1];
+                        if (F::kAParts == 3) *p2 = (T)v[2];
+                        p0 += dpos; p1 += dpos; p2 += dpos;
+                    }
                 }
             }
         }
