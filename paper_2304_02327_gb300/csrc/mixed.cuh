@@ -30,26 +30,25 @@ __device__ __forceinline__ double f2d(float f) {
 // bits (|x - hi - lo| <= 2^-46 |x|), from the bits of x, without FP64 arithmetic.
 // |x| < 2^-103 gives lo = 0; |x| < 2^-126 gives hi = lo = 0; inf/nan map to inf/nan.
 __device__ __forceinline__ void d2ff(double x, float& hi, float& lo) {
+    // branch-free: every case is computed and the right one selected, so a warp never
+    // diverges on the exponent and the elementwise kernels issue no branch here
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const uint32_t s = (uint32_t)(b >> 63) << 31;
     const int e = (int)((b >> 52) & 0x7ff);
     const uint64_t m = b & 0xfffffffffffffull;
     const int ef = e - 896;                     // FP32 exponent field of x
-    if (ef <= 0) { hi = __uint_as_float(s); lo = 0.f; return; }
-    if (ef >= 255) {                            // overflow -> inf; nan stays nan
-        hi = __uint_as_float(s | 0x7f800000u | ((e == 0x7ff && m) ? 0x400000u : 0u));
-        lo = 0.f;
-        return;
-    }
-    hi = __uint_as_float(s | ((uint32_t)ef << 23) | (uint32_t)(m >> 29));
-    if (ef < 24) { lo = 0.f; return; }
+    const uint32_t hn = s | ((uint32_t)ef << 23) | (uint32_t)(m >> 29);
+    // overflow -> inf; nan stays nan
+    const uint32_t hs = s | 0x7f800000u | ((e == 0x7ff && m) ? 0x400000u : 0u);
+    hi = __uint_as_float(ef <= 0 ? s : (ef >= 255 ? hs : hn));
     // remainder = (m mod 2^29) * 2^(e-1075); its top 23 bits as P - Q with
-    // Q = 2^(ef-23-127), P = Q (1 + r/2^23): exact by Sterbenz.
+    // Q = 2^(ef-23-127), P = Q (1 + r/2^23): exact by Sterbenz.  Below FP32's
+    // normal range (ef < 24) and for inf / nan the low part is 0.
     const uint32_t r = (uint32_t)((m & 0x1fffffffull) >> 6);
-    const uint32_t E0 = (uint32_t)(ef - 23);
+    const uint32_t E0 = (uint32_t)(ef - 23) & 0xffu;
     const float P = __uint_as_float((E0 << 23) | r);
     const float Q = __uint_as_float(E0 << 23);
-    lo = __uint_as_float(__float_as_uint(P - Q) | s);
+    lo = __uint_as_float((ef >= 24 && ef < 255) ? (__float_as_uint(P - Q) | s) : 0u);
 }
 
 // Round-to-nearest (ties away) FP32 -> TF32, kept in an FP32 container.

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256, 6) prepass_mixed_kernel(StencilArgsMixed 
 // once and split once into (hi, lo) pairs held in shared memory, the stencil reads
 // its neighbours there (same operations, in the same order, as
 // prepass_mixed_kernel).  d = 2: one 32 x 32 tile and its halo per step of the
-// block loop.  d = 3: a 32 x 16 tile of (i_1, i_2) marches along i_3 through a
+// block loop.  d = 3: a 32 x 32 tile of (i_1, i_2) marches along i_3 through a
 // ring of three planes, so every plane is split once per tile.
 constexpr int kT1 = 32;
 
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(StencilArgsMixed a) {
     }
 }
 
-constexpr int kT2 = 16;      // i_2 extent of a 3D tile
+constexpr int kT2 = 32;      // i_2 extent of a 3D tile
 constexpr int kZ = 32;       // most planes per block of the 3D march
 constexpr int kHalo3 = (kT2 + 2) * (kT1 + 2);      // 612 values of a plane with its halo
 constexpr int kPer3 = (kHalo3 + 255) / 256;         // of them per thread
