@@ -1,7 +1,7 @@
-// Inline-PTX wrappers for sm_103a: mbarriers, bulk async copies (TMA engine),
-// tensor memory (TMEM) and tcgen05 MMAs.  Every wait is bounded: on timeout it
-// raises MM_STATUS_TIMEOUT in the caller's status word and returns false, so no
-// kernel here can spin forever.
+// Inline-PTX wrappers for sm_103a: mbarriers, tensor memory (TMEM), tcgen05
+// commits and loads, and the shared-memory / instruction descriptor encodings.  Every
+// wait is bounded: on timeout it raises MM_STATUS_TIMEOUT in the caller's status word
+// and returns false, so no kernel here can spin forever.
 #pragma once
 
 #include <stdint.h>
@@ -63,21 +63,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     return false;
 }
 
-// 1D bulk copy global -> this CTA's shared memory, completing `bytes` of tx on `bar`.
-// dst and src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-// Make this thread's generic-proxy shared-memory writes visible to the async proxy
-// (the tensor core reads its operands through it).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
 // ---- tensor memory -----------------------------------------------------
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
@@ -102,28 +87,6 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// D[tmem] (+)= A[smem desc] * B[smem desc], kind::tf32, one CTA.
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-// D[tmem] (+)= A[smem desc] * B[smem desc], kind::f16 with BF16 A and B, one CTA.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
 // Arrive on `bar` once all previously issued tcgen05.mma of this thread complete.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -146,38 +109,17 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Round-to-nearest (ties away) FP32 -> TF32, result kept in an FP32 container.
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// Shared-memory matrix descriptor for a K-major operand tile stored with the
-// 128-byte swizzle: rows of 128 bytes, 8-row atoms of 1024 bytes (SBO), the
-// tile base 1024-byte aligned.  `addr` may carry an in-atom K offset (k*32 B).
-__device__ __forceinline__ uint64_t desc_k_sw128(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
-    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: 8-row atom
-    d |= (uint64_t)1 << 46;                            // descriptor version (sm_100 family)
-    d |= (uint64_t)2 << 61;                            // swizzle: 128 B
-    return d;
-}
-
-// The same for the 64-byte swizzle: rows of 64 bytes, 8-row atoms of 512 bytes
-// (SBO), the tile base 512-byte aligned; `addr` may carry an in-row K offset
-// (0 or 32 B, one MMA's K slice).
-__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);          // start address
-    d |= (uint64_t)1 << 16;                            // leading byte offset (unused here)
-    d |= (uint64_t)(512 >> 4) << 32;                   // stride byte offset: 8-row atom
-    d |= (uint64_t)1 << 46;                            // descriptor version (sm_100 family)
-    d |= (uint64_t)4 << 61;                            // swizzle: 64 B
-    return d;
-}
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle (rows of 128 bytes, 8-row atoms of 1024 bytes, the tile base
+// 1024-byte aligned), as two 32-bit words:
+//   low word   start address / 16 (bits 0-13) | leading byte offset 1 (bits 16-29,
+//              unused with this swizzle)
+//   high word  stride byte offset 1024 / 16 (bits 32-45) | descriptor version 1
+//              (bit 46) | swizzle mode 2 = 128 B (bits 61-63)
+// Shared addresses stay below 2^18, so an offset added to the low word (a part
+// tile, or a K slice's 32 bytes = 2 units) never carries out of the address field.
+constexpr uint32_t kDescSw128Hi = (1024u >> 4) | (1u << 14) | (2u << 29);
+__device__ __forceinline__ uint32_t desc_sw128_lo(uint32_t addr) { return ((addr & 0x3FFFFu) >> 4) | (1u << 16); }
 
 // Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
@@ -197,11 +139,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
 
-// Byte offset of element (row, k) (k in 0..31, 4-byte elements) inside a K-major
-// 128B-swizzled tile: 16-byte chunk index XOR (row mod 8).
-__host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k) {
-    return (row >> 3) * 1024u + (row & 7u) * 128u + ((((k >> 2) ^ (row & 7u)) & 7u) << 4) + (k & 3u) * 4u;
-}
 
 }  // namespace tc
 }  // namespace mm

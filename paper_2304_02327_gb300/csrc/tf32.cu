@@ -88,13 +88,12 @@ template <> __device__ __forceinline__ uint32_t idesc_of<FormBF16>(int nc) { ret
 // One thread issues every MMA of the CTA, so its instruction count per MMA bounds
 // the tensor pipe: at ~90 cycles per MMA (per-MMA descriptor arithmetic and
 // predicate set-up) it, not the pipe (N / 2 cycles at N = 160), set the tile time.
-// Here a descriptor is assembled from two 32-bit words: the low word is the start
-// address field (shared-memory address / 16, < 2^14 so an offset never carries out
-// of it) plus the LBO bit, the high word (stride 1024 B, version, 128-byte swizzle)
-// is the same for every operand.  A part tile q starts 16 KB (1024 units) after part
-// 0, B part q at q * bstep units, and K slice kk at 2 kk units (32 bytes).
-constexpr uint32_t kDescHi = (1024u >> 4) | (1u << 14) | (2u << 29);
-__device__ __forceinline__ uint32_t desc_lo(uint32_t addr) { return ((addr & 0x3FFFFu) >> 4) | (1u << 16); }
+// Here each descriptor is assembled from its two 32-bit words (tcgen05.cuh): the
+// low word on the stage base plus a constant offset, the high word shared.  A part
+// tile q starts 16 KB (1024 units) after part 0, B part q at q * bstep units, and
+// K slice kk at 2 kk units (32 bytes).
+constexpr uint32_t kDescHi = tc::kDescSw128Hi;
+__device__ __forceinline__ uint32_t desc_lo(uint32_t addr) { return tc::desc_sw128_lo(addr); }
 
 #define MM_TC_MMA(KIND, D, AOFF, B, BOFF, P)                         \
     "add.u32 la, %1, " AOFF ";\n\t"                                 \
