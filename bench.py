@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nc-cap", type=int, default=0,
+                    help="batched workloads: use this tile width instead of autotuning it "
+                         "(160, 128, 96 or 64; a profiler run then sees the plain run's tiling)")
     return ap.parse_args()
 
 
@@ -245,7 +248,10 @@ def ours_batched(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     plans, gs, Us = api.setup_batch(probs, prec)
-    b = api.Batch(plans, gs, Us, autotune=True, graph=True)
+    if args.nc_cap:
+        b = api.Batch(plans, gs, Us, autotune=False, nc_cap=args.nc_cap, graph=True)
+    else:
+        b = api.Batch(plans, gs, Us, autotune=True, graph=True)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -351,7 +357,7 @@ def ours_batched(args):
         "config": {"workload": args.workload, "instances": len(probs_all), "dof": dof_all,
                    "sizes": "n uniform over {48, 64, ..., 512}, square", "scheme": "expeuler",
                    "tau": probs_all[0].tau, "precision": prec, "size_classes": info["classes"],
-                   "nc_cap_autotuned": info["nc_cap"], "tiles_per_mode": info["tiles_mode1"],
+                   ("nc_cap_pinned" if args.nc_cap else "nc_cap_autotuned"): info["nc_cap"], "tiles_per_mode": info["tiles_mode1"],
                    "graph": "one CUDA graph launch per step (4 kernels)",
                    "l2": "flushed between timed steps (512 MB write); states 0.8 GB > L2",
                    "parallelism": f"LPT shard of instances x{world}"},
