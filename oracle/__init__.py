@@ -26,5 +26,5 @@ Each function's pins (what fixes it independently of itself) live in
 """
 from .phi import expm_pade13, phi_matrices, PADE13_THETA  # noqa: F401
 from .tucker import mode_product, tucker, phisplit_apply  # noqa: F401
-from .integrators import (kron_apply, g_eval, step, integrate,  # noqa: F401
+from .integrators import (kron_apply, g_eval, step, step_at, integrate,  # noqa: F401
                           rel_err_inf, rel_err_fro, OracleProblem)

@@ -35,7 +35,7 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 from .phi import phi_matrices
-from .tucker import mode_product, phisplit_apply
+from .tucker import mode_product, phisplit_apply, phisplit_apply_at
 
 G_NONE, G_CUBIC, G_RICCATI, G_ADR_MANUFACTURED = 0, 1, 2, 3
 EXPEULER, ETD2RK, LAWSON_EULER, LAWSON2B, EXPROSEULER, EXPEULER_ALT = 0, 1, 2, 3, 4, 5
@@ -134,6 +134,30 @@ def step(op: OracleProblem, U: np.ndarray, scheme: int, t: float = 0.0) -> np.nd
         phis = [phi_matrices(tau * J, 1)[1] for J in riccati_jacobian(op, U)]
         return U + tau * phisplit_apply(W, phis, 1)
     raise ValueError(f"unknown scheme {scheme}")
+
+
+def step_at(op: OracleProblem, U: np.ndarray, scheme: int, t: float, index_sets) -> np.ndarray:
+    """The entries of step(op, U, scheme, t) on the grid index_sets[0] x ... x
+    index_sets[d-1] (index_sets[mu-1] lists values of i_mu), for checks on states
+    too large to step in full.  Every tensor the step needs in full -- K U + G(U),
+    and for ETD2RK the first stage U2 and G(U2) - G(U) -- is formed in full; only
+    the last Tucker operator of the step is restricted to the sampled rows of its
+    phi matrices (phisplit_apply_at).  Exponential Euler (eq. (19)), ETD2RK
+    (eq. (20)) and Lawson-Euler (eq. (17)).  Result shape (|I_d|, ..., |I_1|)."""
+    tau = op.tau
+    ix = np.ix_(*[np.asarray(I, dtype=np.int64) for I in reversed(list(index_sets))])
+    if scheme == EXPEULER:
+        W = kron_apply(U, op.A) + g_eval(op, U, t)
+        return U[ix] + tau * phisplit_apply_at(W, op.phi_list(1), 1, index_sets)
+    if scheme == ETD2RK:
+        Gn = g_eval(op, U, t)
+        W1 = kron_apply(U, op.A) + Gn
+        U2 = U + tau * phisplit_apply(W1, op.phi_list(1), 1)
+        W2 = g_eval(op, U2, t + tau) - Gn
+        return U2[ix] + tau * phisplit_apply_at(W2, op.phi_list(2), 2, index_sets)
+    if scheme == LAWSON_EULER:
+        return phisplit_apply_at(U + tau * g_eval(op, U, t), op.phi_list(0), 0, index_sets)
+    raise ValueError(f"step_at: scheme {scheme} not supported")
 
 
 def integrate(op: OracleProblem, U0: np.ndarray, scheme: int, nsteps: int,

@@ -222,3 +222,25 @@ def test_expeuler_alternative_form_exact_for_linear_problems():
     got = integrate(op, U, oi.EXPEULER_ALT, 3)
     ref = scipy.linalg.expm(0.21 * kron_sum(As)) @ vec(U)
     assert np.abs(vec(got) - ref).max() < 1e-12
+
+
+@pytest.mark.parametrize("scheme", [oi.EXPEULER, oi.ETD2RK, oi.LAWSON_EULER])
+@pytest.mark.parametrize("kind", ["adr", "riccati"])
+def test_step_at_is_the_sampled_full_step(scheme, kind):
+    """step_at (one step restricted to a sampled output grid, used on states too large
+    to step in full) equals the full step on that grid, for tensors and for the
+    Riccati form, including sets that skip, repeat no index and end at the edge."""
+    if kind == "adr":
+        p = wl.adr_3d(seed=3, sizes=(9, 7, 6), tau=2e-3)
+        sets = [np.array([0, 3, 8]), np.array([1, 6]), np.array([0, 2, 5])]
+    else:
+        p = wl.riccati_2d(10, seed=4, tau=1e-3)
+        p.u0 = 0.1 * wl.random_tensor((10, 10), 5)
+        sets = [np.array([0, 4, 9]), np.array([2, 3, 7, 9])]
+    op = OracleProblem.from_problem(p)
+    U = np.asarray(p.u0, dtype=np.float64)
+    full = oi.step(op, U, scheme, 0.25)
+    got = oi.step_at(op, U, scheme, 0.25, sets)
+    ref = full[np.ix_(*reversed(sets))]
+    assert got.shape == ref.shape
+    assert np.abs(got - ref).max() <= 1e-14 * np.abs(full).max()

@@ -6,8 +6,10 @@ that cannot afford cudaMalloc's synchronisation, a plug-in barred from the CUDA
 allocator).  It keeps its intermediate tensor in a fixed array built into the
 library instead of a caller workspace.  This test calls it through the C ABI
 twice in a row and checks each result against mumode_phi_apply, the entry point
-that uses caller-provided workspace, within the FP64 tolerance of the other
-parity tests (1e-12 relative).  The file is named to be collected last.
+that uses caller-provided workspace, and against the FP64 oracle's split action
+(oracle.tucker.phisplit_apply with the oracle's own phi matrices), within the FP64
+tolerance of the other parity tests (1e-12 relative).  The file is named to be
+collected last.
 """
 import ctypes
 import math
@@ -16,6 +18,8 @@ import numpy as np
 import pytest
 import torch
 
+from oracle.phi import phi_matrices
+from oracle.tucker import phisplit_apply
 from paper_2304_02327_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +63,12 @@ def rel_err(a, b):
     return float((a - b).abs().max() / b.abs().max())
 
 
+def oracle_apply(As, tau, ell, V, alpha):
+    """alpha P_l^(2) V from the oracle's phi matrices (Pade route), as a tensor."""
+    ref = alpha * phisplit_apply(V.cpu().numpy(), [phi_matrices(tau * A, ell)[ell] for A in As], ell)
+    return torch.from_numpy(ref)
+
+
 def test_noalloc_matches_workspace_entry_point_two_calls(api):
     # call 1: the 3D ADR operator at n = 128 (N = 2^21, the largest accepted size)
     p = wl.adr_3d(n=128, seed=2, steps=1)
@@ -68,6 +78,8 @@ def test_noalloc_matches_workspace_entry_point_two_calls(api):
     ref1 = api.mumode_phi_apply(plan, 1, V1, alpha=0.5)
     torch.cuda.synchronize()
     assert rel_err(got1, ref1) <= TOL
+    orc1 = oracle_apply(p.A, p.tau, 1, V1, 0.5)
+    assert rel_err(got1.cpu(), orc1) <= TOL
     # call 2 right after, different sizes, phi index and input: the shared
     # scratch still holds call 1's data and must not leak into the result
     ns = (37, 20, 9)
@@ -78,8 +90,10 @@ def test_noalloc_matches_workspace_entry_point_two_calls(api):
     ref2 = api.mumode_phi_apply(plan2, 2, V2, alpha=-1.5)
     torch.cuda.synchronize()
     assert rel_err(got2, ref2) <= TOL
+    assert rel_err(got2.cpu(), oracle_apply(As, 2e-3, 2, V2, -1.5)) <= TOL
     # and the first result is unchanged by the second call
     assert rel_err(got1, ref1) <= TOL
+    assert rel_err(got1.cpu(), orc1) <= TOL
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(api):
