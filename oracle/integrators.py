@@ -87,10 +87,15 @@ def g_eval(op: OracleProblem, U: np.ndarray, t: float = 0.0) -> np.ndarray:
         c0, c1, c2, c3 = op.cubic
         return c0 + c1 * U + c2 * U * U + c3 * U * U * U
     if op.g_kind == G_RICCATI:
-        # Stored arrays are (n_2, n_1) = transposes of the n_1 x n_2 matrices.
-        Um = U.T
-        Cm = op.C.T
-        return np.ascontiguousarray((Cm + Um @ op.B @ Um).T)
+        # The state is the matrix U whose column-stacked vec is the tensor's (Section
+        # 1): rows = the first d/2 directions, columns = the rest (d = 2: n_1 x n_2;
+        # d = 4, the order-4 form of the Section 4.1 remark: n_1 n_2 x n_3 n_4).
+        # Stored arrays are C-ordered (n_d, ..., n_1), i.e. transposes of the matrices.
+        m1 = int(np.prod(U.shape[U.ndim // 2:]))
+        m2 = U.size // m1
+        Um = U.reshape(m2, m1).T
+        Cm = op.C.reshape(m2, m1).T
+        return np.ascontiguousarray((Cm + Um @ op.B @ Um).T).reshape(U.shape)
     if op.g_kind == G_ADR_MANUFACTURED:
         et = np.exp(t)
         return (1.0 / (1.0 + U * U) + et * op.psi_a

@@ -129,10 +129,11 @@ int plain_gemm(int M, int N, int K, const double* A, int64_t lda, const double* 
     return launch_dgemm(g, e, s);
 }
 
-// Riccati G(U) = C + (U B) U (eq. (2)) with U n1 x n2: XB = U B, G = XB U + C + gamma*D2.
+// Riccati G(U) = C + (U B) U (eq. (2)) with U the n1 x n2 matrix view (column-major,
+// n1 = riccati_rows): XB = U B, G = XB U + C + gamma*D2.
 int riccati_g(const mm_plan_s* p, const mm_nonlin* g, const double* U, double* XB, double* G,
               const double* D2, double gamma, cudaStream_t s) {
-    const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+    const int n1 = (int)riccati_rows(p), n2 = (int)(p->N / n1);
     int rc = plain_gemm(n1, n1, n2, U, n1, g->B, n2, XB, n1, nullptr, 0, nullptr, 0, s);
     if (rc) return rc;
     return plain_gemm(n1, n2, n1, XB, n1, U, n1, G, n1, g->C, 1.0, D2, gamma, s);
@@ -315,8 +316,8 @@ extern "C" size_t expint_workspace_bytes(mm_plan p, int scheme, const mm_nonlin*
     if (scheme == MM_EXPEULER_ALT) buffers = 3;  // + the first Tucker's result
     if (scheme == MM_LAWSON2B) buffers = 4;      // + Z, U2
     size_t elems = buffers * N;
-    if (g && g->kind == MM_G_RICCATI && p->d == 2) {
-        const size_t n1 = (size_t)p->n[0];
+    if (g && g->kind == MM_G_RICCATI && p->d % 2 == 0) {
+        const size_t n1 = (size_t)riccati_rows(p);
         elems += N + (n1 * n1 > N ? n1 * n1 : N);  // Gn, XB
     }
     if (scheme == MM_EXPROSEULER && p->d == 2) elems += rosenbrock_extra(p);
@@ -333,10 +334,14 @@ extern "C" int expint_step(mm_plan p, int scheme, const mm_nonlin* g, double* U,
     const int gk = g ? g->kind : MM_G_NONE;
     if (gk < MM_G_NONE || gk > MM_G_ADR_MANUFACTURED) return MM_ERR_ARG;
     if (gk == MM_G_RICCATI) {
-        if (p->d != 2 || !g->B || !g->C) return MM_ERR_ARG;
+        // the state must have a matrix view: an even number of directions
+        if (p->d % 2 != 0 || !g->B || !g->C) return MM_ERR_ARG;
+        if (riccati_rows(p) > 0x7fffffffLL || p->N / riccati_rows(p) > 0x7fffffffLL) return MM_ERR_SHAPE;
         if (scheme != MM_EXPEULER && scheme != MM_ETD2RK && scheme != MM_EXPROSEULER) return MM_ERR_UNSUPPORTED;
     }
-    if (scheme == MM_EXPROSEULER && (gk != MM_G_RICCATI || p->prec != MM_FP64)) return MM_ERR_UNSUPPORTED;
+    // the Jacobian A + dG is a Kronecker sum only in the two-direction form
+    if (scheme == MM_EXPROSEULER && (gk != MM_G_RICCATI || p->prec != MM_FP64 || p->d != 2))
+        return MM_ERR_UNSUPPORTED;
     if (scheme == MM_EXPEULER_ALT && (gk == MM_G_RICCATI || p->prec != MM_FP64)) return MM_ERR_UNSUPPORTED;
     if (gk == MM_G_ADR_MANUFACTURED && (!g->psi_a || !g->psi_b)) return MM_ERR_ARG;
     const size_t need = expint_workspace_bytes(p, scheme, g);

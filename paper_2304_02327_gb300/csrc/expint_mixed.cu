@@ -10,7 +10,8 @@
 // ETD2RK, writes the split stage-2 input g(U2) - g(U) (formed in FP32 from its
 // difference expansion).
 //
-// Dense A_mu and the Riccati G (d = 2, U n1 x n2 column-major, Section 1 eq. (2)):
+// Dense A_mu (d = 2) and the Riccati G (even d; U the n1 x n2 column-major matrix view
+// of the state, n1 the product of the first d/2 sizes; Section 1 eq. (2)):
 // K u is split into the tridiagonal band of each A_mu, evaluated by the stencil
 // prepass from differences of the state, plus the remainders R_mu = A_mu - band:
 //   R1 U = X M^T with X = R1, M = U^T;    U R2^T with X = U, M = R2,
@@ -178,7 +179,7 @@ MixedWs carve_ws(const mm_plan_s* p, bool dense, uint8_t* base) {
     w.pairs = (float2*)c.take(8 * N);
     w.U2 = (double*)c.take(8 * N);
     if (dense) {
-        const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+        const int n1 = (int)riccati_rows(p), n2 = (int)(p->N / n1);
         w.Ut = c.take(matrix_parts_bytes(p->prec, n1, n2, 3));
         w.Un = c.take(matrix_parts_bytes(p->prec, n2, n1, 3));
         w.T = c.take(matrix_parts_bytes(p->prec, n1, n1, 3));
@@ -194,7 +195,7 @@ MixedWs carve_ws(const mm_plan_s* p, bool dense, uint8_t* base) {
 int dense_products(mm_plan_s* p, const double* U, bool rem, bool ubu, float* yk, float* yq, const MixedWs& w,
                    cudaStream_t s) {
     const int prec = p->prec;
-    const int n1 = (int)p->n[0], n2 = (int)p->n[1];
+    const int n1 = (int)riccati_rows(p), n2 = (int)(p->N / n1);
     const PartView Ut = matrix_view(prec, w.Ut, n1, n2);     // M = U   (rows i1, k = i2)
     const PartView Un = matrix_view(prec, w.Un, n2, n1);     // M = U^T (rows i2, k = i1)
     int rc = split_matrix(prec, U, n1, 1, 0, Ut, 3, s);
@@ -264,7 +265,8 @@ int mixed_expint(mm_plan_s* p, int scheme, const mm_nonlin* gd, double* U, doubl
                  uint8_t* ws, cudaStream_t s) {
     const bool riccati = gd && gd->kind == MM_G_RICCATI;
     const bool dense = !p->tridiag || riccati;
-    if (dense && (p->d != 2 || (!p->tridiag && !p->rem_split[0]))) return MM_ERR_UNSUPPORTED;
+    if (!p->tridiag && (p->d != 2 || !p->rem_split[0])) return MM_ERR_UNSUPPORTED;
+    if (riccati && p->d % 2 != 0) return MM_ERR_UNSUPPORTED;
     if (riccati && scheme != MM_EXPEULER && scheme != MM_ETD2RK) return MM_ERR_UNSUPPORTED;
     const PointwiseG pg = pointwise_of(gd);
     const MixedWs w = carve_ws(p, dense, ws);
@@ -278,8 +280,8 @@ int mixed_expint(mm_plan_s* p, int scheme, const mm_nonlin* gd, double* U, doubl
     const int64_t N = p->N;
     int rc = MM_OK;
     if (riccati) {   // X = B^T: B is n2 x n1 column-major
-        rc = split_matrix(p->prec, gd->B, p->n[1], 0, 0, matrix_view(p->prec, w.Bx, p->n[0], (int)p->n[1]),
-                          form_parts(p->prec), s);
+        const int64_t m1 = riccati_rows(p), m2 = p->N / m1;    // B is m2 x m1
+        rc = split_matrix(p->prec, gd->B, m2, 0, 0, matrix_view(p->prec, w.Bx, m1, (int)m2), form_parts(p->prec), s);
         if (rc) return rc;
     }
     const double tau = p->tau;

@@ -57,6 +57,13 @@ struct mm_plan_s {
 };
 
 namespace mm {
+// Rows of the matrix view of a state for the Riccati term: the first d/2 directions
+// (d = 2: U is n1 x n2; d = 4, the order-4 form of the LQ problem: n1 n2 x n3 n4).
+inline int64_t riccati_rows(const mm_plan_s* p) {
+    int64_t m = 1;
+    for (int mu = 0; mu < p->d / 2; ++mu) m *= p->n[mu];
+    return m;
+}
 // Builds the TF32x3 operand images of the plan's phi matrices (tf32.cu).
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s);
 // phi_0 .. phi_L of tau*A (n x n, column-major, device) into out[0..L] by scaling,

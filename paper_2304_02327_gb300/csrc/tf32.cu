@@ -19,9 +19,9 @@
 //           a0 b0 | a1 b0 + a0 b1 + a2 b0 + a1 b1 + a0 b2
 // The tensor cores' FP32 accumulation truncates toward zero, which biases long
 // sums (measured: a one-sided relative error growing with K).  So the main
-// product of every kGroup = 2 K-blocks goes into a fresh TMEM slot (only its eight
-// MMAs accumulate in hardware) and the epilogue warps add the slots into FP32
-// registers with round-to-nearest; the much smaller corrections accumulate in TMEM
+// product of every K-block goes into a fresh TMEM slot (only its four MMAs
+// accumulate in hardware) and the epilogue warps add the slots into FP32 registers
+// with round-to-nearest; the much smaller corrections accumulate in TMEM
 // over the whole tile, in an accumulator of their own: added onto the main product,
 // their low-order bits would force a truncation at main-product magnitude into sums
 // that are otherwise exact (an exactly representable operand, such as the 0/alpha
@@ -68,7 +68,11 @@ constexpr int kRows = 128;                 // MMA M / rows per tile
 constexpr uint32_t kRowBytes = 128;        // one stage's K slice of a row (128-byte swizzle)
 constexpr uint32_t kATile = kRows * kRowBytes;   // bytes of one operand part tile
 constexpr int kMaxStages = 4;
-constexpr int kGroup = 2;                  // stages whose main products share a TMEM slot
+// Stages whose main products share a TMEM slot.  Measured on the 100-step 3D ADR run
+// at n = 320: with 2, the truncation bias of the slot sums took the TF32x3 form to
+// 1.16e-6 (BF16x3 8.8e-7) of the FP64 run; with 1, 5.5e-7 (5.6e-7), for ~7 % of
+// contraction time.
+constexpr int kGroup = 1;
 constexpr int kBParts = 3;                 // Phi = b0 + b1 + b2 in both forms
 constexpr int kNcMax = 160;                // [main slot 0 | main slot 1 | corr] fit 512 TMEM columns
 constexpr int kBars = 2 * kMaxStages + 9;  // full, empty per stage; main full/empty (slot);

@@ -158,40 +158,68 @@ def riccati_2d(n: int = 2048, seed: int = 5, tau: float = 1e-4, steps: int = 50,
                    steps=steps, scheme=scheme)
 
 
+def lq_operators(nhat: int, alpha: float = 100.0):
+    """The pieces of the paper's linear-quadratic control problem (Section 4.1).
+
+    On the inner nhat x nhat grid x_i = i h, h = 1/(nhat + 1), with homogeneous
+    Dirichlet conditions and second-order centred differences:
+      D1 = discretisation of d_xx - 10 x d_x,   D2 = of d_yy - 100 y d_y (nhat x nhat),
+      A  = I (x) D1 + D2 (x) I (n x n, n = nhat^2, unknown k = i + (j - 1) nhat),
+    b_k = 1 where 0.1 < x_i <= 0.3, c_k = 1 where 0.7 < x_i <= 0.9, B = -b b^T,
+    C = alpha c^T c.  Returns (D1, D2, A, B, C)."""
+    h = 1.0 / (nhat + 1)
+    x = grid(nhat)
+
+    def d1(coef):
+        D = np.zeros((nhat, nhat))
+        for i in range(nhat):
+            D[i, i] = -2.0 / h ** 2
+            if i > 0:
+                D[i, i - 1] = 1.0 / h ** 2 + coef * x[i] / (2 * h)
+            if i < nhat - 1:
+                D[i, i + 1] = 1.0 / h ** 2 - coef * x[i] / (2 * h)
+        return D
+
+    D1, D2 = d1(10.0), d1(100.0)
+    I = np.eye(nhat)
+    A = np.kron(I, D1) + np.kron(D2, I)
+    xi = np.tile(x, nhat)                                # x_i of unknown k
+    b = ((xi > 0.1) & (xi <= 0.3)).astype(np.float64)
+    c = ((xi > 0.7) & (xi <= 0.9)).astype(np.float64)
+    return D1, D2, A, -np.outer(b, b), alpha * np.outer(c, c)
+
+
 def lq_riccati(nhat: int = 30, steps: int = 170, scheme: int = ETD2RK, T: float = 0.025,
                alpha: float = 100.0) -> Problem:
     """The paper's linear-quadratic control problem (Section 4.1), no random input.
 
-    A (n x n, n = nhat^2) discretises d_xx + d_yy - 10 x d_x - 100 y d_y on [0,1]^2
-    with homogeneous Dirichlet conditions by second-order centred differences on the
-    inner grid x_i = i h, h = 1/(nhat + 1), unknown k = i + (j - 1) nhat (x fastest);
-    b_k = 1 where 0.1 < x_i <= 0.3, c_k = 1 where 0.7 < x_i <= 0.9, C = alpha c^T c,
-    B = -b b^T, U0 = 0.  The Riccati equation U' = A^T U + U A + C + U B U is the
+    A (n x n, n = nhat^2) discretises d_xx + d_yy - 10 x d_x - 100 y d_y (see
+    lq_operators); U0 = 0.  The Riccati equation U' = A^T U + U A + C + U B U is the
     two-direction form with A_1 = A_2 = A^T; tau = T / steps.
     """
-    h = 1.0 / (nhat + 1)
-    x = grid(nhat)
+    _, _, A, B, Cm = lq_operators(nhat, alpha)
     n = nhat * nhat
-    A = np.zeros((n, n))
-    for j in range(nhat):
-        for i in range(nhat):
-            k = i + j * nhat
-            A[k, k] = -4.0 / h ** 2
-            if i > 0:
-                A[k, k - 1] = 1.0 / h ** 2 + 10.0 * x[i] / (2 * h)
-            if i < nhat - 1:
-                A[k, k + 1] = 1.0 / h ** 2 - 10.0 * x[i] / (2 * h)
-            if j > 0:
-                A[k, k - nhat] = 1.0 / h ** 2 + 100.0 * x[j] / (2 * h)
-            if j < nhat - 1:
-                A[k, k + nhat] = 1.0 / h ** 2 - 100.0 * x[j] / (2 * h)
-    xi = np.tile(x, nhat)                                # x_i of unknown k
-    b = ((xi > 0.1) & (xi <= 0.3)).astype(np.float64)
-    c = ((xi > 0.7) & (xi <= 0.9)).astype(np.float64)
-    B = -np.outer(b, b)
-    Cm = alpha * np.outer(c, c)
     return Problem(name=f"lq_riccati_nhat{nhat}", A=[A.T.copy(), A.T.copy()], u0=np.zeros((n, n)),
                    g_kind=G_RICCATI, B=B, C=np.ascontiguousarray(Cm.T), tau=T / steps,
+                   steps=steps, scheme=scheme)
+
+
+def lq_riccati_order4(nhat: int = 30, steps: int = 170, scheme: int = ETD2RK, T: float = 0.025,
+                      alpha: float = 100.0) -> Problem:
+    """The same LQ problem in the order-4 tensor form of the remark closing Section 4.1.
+
+    A^T = I (x) D1^T + D2^T (x) I is itself a Kronecker sum, so A^T U + U A is the
+    four-direction Kronecker sum K = A_4 (+) A_3 (+) A_2 (+) A_1 with A_1 = A_3 = D1^T
+    and A_2 = A_4 = D2^T (nhat x nhat each) acting on U as an nhat^4 tensor: i_1, i_2
+    the x and y indices of the matrix row k = i_1 + nhat i_2, i_3, i_4 those of the
+    column.  The state's memory layout is the two-direction form's (the column-major
+    n x n matrix); G(U) = C + U B U is formed on that matrix view.
+    """
+    D1, D2, _, B, Cm = lq_operators(nhat, alpha)
+    sh = (nhat,) * 4
+    return Problem(name=f"lq_riccati_order4_nhat{nhat}",
+                   A=[D1.T.copy(), D2.T.copy(), D1.T.copy(), D2.T.copy()], u0=np.zeros(sh),
+                   g_kind=G_RICCATI, B=B, C=np.ascontiguousarray(Cm.T).reshape(sh), tau=T / steps,
                    steps=steps, scheme=scheme)
 
 
@@ -276,6 +304,9 @@ def workload(name: str, **over) -> Problem:
         # the paper's LQ-control problem (Section 4.1), nhat = 30, T = 0.025, 170 steps
         "lq_riccati_nhat30_etd2rk": lambda: lq_riccati(30, 170, ETD2RK),
         "lq_riccati_nhat30_exprosenbrock": lambda: lq_riccati(30, 170, EXPROSEULER),
+        # the same problem as an order-4 tensor with the 30 x 30 matrices D1^T, D2^T
+        # (the remark closing Section 4.1)
+        "lq_riccati_order4_nhat30_etd2rk": lambda: lq_riccati_order4(30, 170, ETD2RK),
     }
     if name in BATCHED:
         raise ValueError(f"{name} is a batch: use batched_workload()")

@@ -248,7 +248,7 @@ def lq_ref():
     extrapolation of ETD2RK at 170 and 340 steps, plus the printed errors."""
     from tests.test_oracle_paper import lq_golden, lq_reference
     ref, _ = lq_reference(30, 170)
-    return ref, {(s, n): e for (_, s, n, e) in lq_golden()}
+    return ref, {(s, n): e for (_, s, n, e) in lq_golden(30)}
 
 
 @pytest.mark.parametrize("scheme,prec", [(wl.ETD2RK, "fp64"), (wl.EXPROSEULER, "fp64"),
@@ -282,3 +282,79 @@ def test_checkpoint_resume_is_bit_identical_fp64(api):
     api.expint_step(plan3, p.scheme, W, 2, t0=4 * p.tau, g=g3)   # time-dependent g
     torch.cuda.synchronize()
     assert torch.equal(U, W)
+
+
+@pytest.mark.parametrize("scheme", [wl.EXPEULER, wl.ETD2RK])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("bf16x3", 1e-6), ("tf32x3", 1e-6)])
+def test_lq_order4_matches_oracle(api, scheme, prec, tol):
+    """The LQ problem as an order-4 tensor (the remark closing Section 4.1): four
+    directions of nhat x nhat matrices D1^T, D2^T, D1^T, D2^T, and G = C + U B U on the
+    matrix view of the state, against the oracle's order-4 run."""
+    p = wl.lq_riccati_order4(8, 12, scheme)
+    plan, g, U = api.setup(p, prec)
+    api.expint_step(plan, scheme, U, p.steps, g=g)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    ref = integrate(OracleProblem.from_problem(p), p.u0, scheme, p.steps)
+    got = U.cpu().numpy()
+    assert rel_err_fro(got, ref) <= tol and rel_err_inf(got, ref) <= tol
+
+
+def test_lq_order4_nhat30_converges_to_the_lq_solution(api, lq_ref):
+    """The order-4 form of the paper's LQ problem (nhat = 30: four 30 x 30 phi
+    matrices per phi-function instead of two 900 x 900 ones), FP64 on the GPU, against
+    the two-direction form's extrapolated solution: the GPU's errors at 30 and 65
+    steps are the oracle's order-4 errors (about 2.3e-4 and 4.8e-5, the size of the
+    two-direction form's printed 1.72e-4 and 3.53e-5) and fall at second order."""
+    ref, printed = lq_ref
+    errs, oracle_errs = [], []
+    for m in (30, 65):
+        p = wl.lq_riccati_order4(30, m, wl.ETD2RK)
+        plan, g, U = api.setup(p, "fp64")
+        api.expint_step(plan, wl.ETD2RK, U, m, g=g)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        errs.append(rel_err_fro(U.cpu().numpy().reshape(ref.shape), ref))
+        orc = integrate(OracleProblem.from_problem(p), p.u0, wl.ETD2RK, m)
+        oracle_errs.append(rel_err_fro(orc.reshape(ref.shape), ref))
+    order = math.log(errs[0] / errs[1]) / math.log(65 / 30)
+    assert 1.9 < order < 2.2, (errs, order)
+    for e, o in zip(errs, oracle_errs):
+        assert abs(e / o - 1) < 1e-4, (errs, oracle_errs)
+    assert 0.5 < errs[0] / printed[("etd2rk", 30)] < 2, errs
+
+
+def test_rosenbrock_needs_the_two_direction_form(api):
+    p = wl.lq_riccati_order4(6, 4, wl.EXPROSEULER)
+    plan, g, U = api.setup(p, "fp64")
+    with pytest.raises(api.PhisplitError):
+        api.expint_step(plan, wl.EXPROSEULER, U, 1, g=g)
+
+
+@pytest.fixture(scope="module")
+def lq40_ref():
+    """The paper's LQ problem at nhat = 40 (n = 1600) at T = 0.025 from the oracle on
+    the host cores: Richardson extrapolation of ETD2RK at 100 and 200 steps, plus the
+    printed errors of Figure "riccati_40"."""
+    from tests.test_oracle_paper import lq_golden, lq_reference
+    ref, _ = lq_reference(40, 100)
+    return ref, {(s, n): e for (_, s, n, e) in lq_golden(40)}
+
+
+@pytest.mark.parametrize("scheme,prec,steps", [(wl.ETD2RK, "fp64", 30), (wl.ETD2RK, "fp64", 65),
+                                               (wl.EXPROSEULER, "fp64", 30), (wl.ETD2RK, "bf16x3", 30),
+                                               (wl.ETD2RK, "tf32x3", 65)])
+def test_lq_riccati_nhat40_reproduces_printed_errors(api, lq40_ref, scheme, prec, steps):
+    """GPU runs of the paper's LQ problem at nhat = 40 (Section 4.1, Table
+    "riccati_order_40") land on the errors printed in Figure "riccati_40" (ETD2RK
+    1.9744e-4 at 30 steps and 4.0443e-5 at 65, exponential Rosenbrock-Euler 1.7195e-4
+    at 30) to 0.5 %."""
+    ref, printed = lq40_ref
+    p = wl.lq_riccati(40, steps, scheme)
+    plan, g, U = api.setup(p, prec)
+    api.expint_step(plan, scheme, U, steps, g=g)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    e = rel_err_fro(U.cpu().numpy(), ref)
+    key = ("etd2rk" if scheme == wl.ETD2RK else "exprosenbrock", steps)
+    assert abs(e / printed[key] - 1) < 5e-3, (e, printed[key])

@@ -244,3 +244,51 @@ def test_step_at_is_the_sampled_full_step(scheme, kind):
     ref = full[np.ix_(*reversed(sets))]
     assert got.shape == ref.shape
     assert np.abs(got - ref).max() <= 1e-14 * np.abs(full).max()
+
+
+def _lq_pair(nhat, steps, scheme):
+    p2 = wl.lq_riccati(nhat, steps, scheme)
+    p4 = wl.lq_riccati_order4(nhat, steps, scheme)
+    return p2, p4, OracleProblem.from_problem(p2), OracleProblem.from_problem(p4)
+
+
+def test_lq_order4_operator_is_the_two_direction_operator():
+    """The remark closing Section 4.1: A^T U + U A of the LQ problem is the order-4
+    Kronecker sum of D1^T, D2^T, D1^T, D2^T on the same memory, and G = C + U B U
+    is the same function of the state in both forms."""
+    nhat = 5
+    p2, p4, op2, op4 = _lq_pair(nhat, 10, oi.ETD2RK)
+    U2 = 0.1 * wl.random_tensor((nhat * nhat, nhat * nhat), 3)
+    U4 = U2.reshape((nhat,) * 4)
+    K2, K4 = kron_apply(U2, p2.A), kron_apply(U4, p4.A)
+    assert np.abs(K4.reshape(U2.shape) - K2).max() <= 1e-12 * np.abs(K2).max()
+    G2, G4 = g_eval(op2, U2), g_eval(op4, U4)
+    assert np.abs(G4.reshape(U2.shape) - G2).max() <= 1e-14 * np.abs(G2).max()
+
+
+def test_lq_order4_lawson_step_equals_two_direction_form():
+    """For l = 0 the direction split is exact (eq. (5)-(6)): a Lawson-Euler step of the
+    order-4 form (four 6 x 6 exponentials) equals that of the two-direction form
+    (two 36 x 36 exponentials)."""
+    nhat = 6
+    p2, p4, op2, op4 = _lq_pair(nhat, 20, oi.LAWSON_EULER)
+    U2 = 0.05 * wl.random_tensor((nhat * nhat, nhat * nhat), 4)
+    a = oi.step(op2, U2, oi.LAWSON_EULER)
+    b = oi.step(op4, U2.reshape((nhat,) * 4), oi.LAWSON_EULER).reshape(U2.shape)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+
+
+def test_lq_order4_etd2rk_converges_at_order_two_to_the_same_solution():
+    """The order-4 form splits phi_1, phi_2 over four directions instead of two, so
+    its ETD2RK differs from the two-direction form's by O(tau^2) per unit time; both
+    converge at order two to the same solution (a fine two-direction run here)."""
+    nhat = 6
+    p, _, op, _ = _lq_pair(nhat, 400, oi.ETD2RK)
+    ref = integrate(op, p.u0, oi.ETD2RK, 400)
+    errs = []
+    for m in (10, 20, 40):
+        p4 = wl.lq_riccati_order4(nhat, m, oi.ETD2RK)
+        got = integrate(OracleProblem.from_problem(p4), p4.u0, oi.ETD2RK, m)
+        errs.append(oi.rel_err_fro(got.reshape(ref.shape), ref))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(1.8 < o < 2.3 for o in orders), (errs, orders)

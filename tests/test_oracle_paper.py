@@ -68,13 +68,28 @@ def test_oracle_reproduces_paper_error(sizes, scheme, steps, err):
     assert abs(got - err) <= 1e-8 * err, (got, err)
 
 
-def lq_golden():
+def lq_golden(nhat=None):
+    """Rows (nhat, scheme, steps, error) of the printed LQ errors, of one nhat if given."""
     rows = []
     for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_lq_riccati_errors.txt")):
         if line.strip() and not line.startswith("#"):
-            nhat, scheme, steps, err = line.split()
-            rows.append((int(nhat), scheme, int(steps), float(err)))
+            nh, scheme, steps, err = line.split()
+            if nhat is None or int(nh) == nhat:
+                rows.append((int(nh), scheme, int(steps), float(err)))
     return rows
+
+
+def test_lq_golden_file_complete():
+    rows = lq_golden()
+    assert len(rows) == 20
+    for nhat in (30, 40):
+        r = lq_golden(nhat)
+        assert sorted({x[2] for x in r}) == [30, 65, 100, 135, 170]
+        assert {x[1] for x in r} == {"etd2rk", "exprosenbrock"}
+        # the printed errors fall with the step count (second order)
+        for sch in ("etd2rk", "exprosenbrock"):
+            e = [x[3] for x in sorted(r) if x[1] == sch]
+            assert all(a > b for a, b in zip(e, e[1:]))
 
 
 def lq_reference(nhat, n_coarse):
@@ -92,10 +107,23 @@ def test_lq_riccati_printed_error():
     the printed errors (Figure "riccati"): against a reference extrapolated from 170
     and 340 steps, the 340-step solution's error is a quarter of the printed 170-step
     error (second order), and the 30-step error is the printed 1.7186e-4 to 0.3 %."""
-    printed = {(s, n): e for (_, s, n, e) in lq_golden()}
+    printed = {(s, n): e for (_, s, n, e) in lq_golden(30)}
     ref, gap = lq_reference(30, 170)
     assert abs(gap / (printed[("etd2rk", 170)] / 4) - 1) < 0.05, gap
     p = wl.lq_riccati(30, 30, wl.ETD2RK)
     got = integrate(OracleProblem.from_problem(p), p.u0, wl.ETD2RK, 30)
     e = rel_err_fro(got, ref)
     assert abs(e / printed[("etd2rk", 30)] - 1) < 3e-3, e
+
+
+@pytest.mark.slow
+def test_lq_riccati_nhat40_printed_error():
+    """nhat = 40 (n = 1600): the oracle's ETD2RK at 30 steps reproduces the printed
+    1.9744e-4 of Figure "riccati_40" against a reference extrapolated from 100 and 200
+    steps (several minutes of host BLAS, hence slow)."""
+    printed = {(s, n): e for (_, s, n, e) in lq_golden(40)}
+    ref, gap = lq_reference(40, 100)
+    p = wl.lq_riccati(40, 30, wl.ETD2RK)
+    got = integrate(OracleProblem.from_problem(p), p.u0, wl.ETD2RK, 30)
+    e = rel_err_fro(got, ref)
+    assert abs(e / printed[("etd2rk", 30)] - 1) < 5e-3, e
