@@ -84,7 +84,7 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "bf16x3"],
                     help="form of the headline value")
     ap.add_argument("--mixed", default="bf16x3,tf32x3",
-                    help="further forms recorded beside the headline ('' for none)")
+                    help="further forms recorded beside the headline ('none' for none)")
     ap.add_argument("--batch", default=DEFAULT_BATCH,
                     help="batched workload recorded beside the headline ('none' to skip)")
     ap.add_argument("--batch-prec", default="bf16x3", choices=["tf32x3", "bf16x3"])
@@ -750,7 +750,7 @@ def ours(args):
     p = wl.workload(args.workload)
     p.name_tag = args.workload
     head = time_single(api, p, args.prec, args, flush, stream, world, local, do_e2e=True)
-    forms = [f for f in (x.strip() for x in args.mixed.split(",")) if f and f != args.prec]
+    forms = [f for f in (x.strip() for x in args.mixed.split(",")) if f and f != "none" and f != args.prec]
     mixed = {}
     for prec in forms:
         r = time_single(api, p, prec, args, flush, stream, world, local, do_e2e=True)

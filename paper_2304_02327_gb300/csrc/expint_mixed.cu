@@ -31,6 +31,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "forms.cuh"
 #include "mixed.cuh"
@@ -123,6 +124,104 @@ __global__ void __launch_bounds__(256) mixed_update_kernel(const float* __restri
             if (i < N) update_one(e, i, yv[k], uv[k], N, alphaf, t0f, t1f);
         }
     }
+}
+
+// The same epilogue for the common case of 16-byte aligned arrays and N a multiple
+// of 4: each thread takes four consecutive elements with 16-byte loads and stores
+// (y as one float4, the states as two double2), the kind and the form are template
+// parameters, and for ETD2RK stage 1 with unpadded fibres (p_1 = n_1, the stage-2
+// input's positions are the elements' own) the parts go out as one vector per part.
+// Element for element the arithmetic of update_one.
+template <class F, int KIND>
+__global__ void __launch_bounds__(256) update4_kernel(const float* __restrict__ y, Epi e, int64_t N, float alphaf,
+                                                      float t0f, float t1f) {
+    using PT = typename std::conditional<F::kElem == 4, uint32_t, uint16_t>::type;
+    const double* src = (KIND == EPI_ETD_S2 || KIND == EPI_LAWSON2) ? e.U2 : e.U;
+    const int64_t N4 = N >> 2;
+    const bool flat = e.w2_p == e.w2_n;
+    bool bad = false;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N4; g += (int64_t)gridDim.x * blockDim.x) {
+        const float4 yq = __ldg((const float4*)y + g);
+        const float yv[4] = {yq.x, yq.y, yq.z, yq.w};
+        double uv[4] = {0.0, 0.0, 0.0, 0.0};
+        if (KIND != EPI_STORE) {
+            const double2 a = __ldg((const double2*)src + 2 * g), b = __ldg((const double2*)src + 2 * g + 1);
+            uv[0] = a.x; uv[1] = a.y; uv[2] = b.x; uv[3] = b.y;
+        }
+        const int64_t i0 = 4 * g;
+        double out[4];
+        uint32_t parts[4][3];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (KIND == EPI_STORE) {
+                out[j] = e.alpha * mx::f2d(yv[j]);
+            } else if (KIND == EPI_EE || KIND == EPI_ETD_S2 || KIND == EPI_ETD_S1 || KIND == EPI_ETD_S1_NOG) {
+                out[j] = fma(e.alpha, mx::f2d(yv[j]), uv[j]);
+            } else {   // EPI_LAWSON2
+                float uh, ul;
+                mx::d2ff(uv[j], uh, ul);
+                const float gv = (float)e.beta * mx::g32(e.g, uh + ul, t1f, i0 + j);
+                out[j] = fma(e.alpha, mx::f2d(yv[j]), mx::f2d(gv));
+            }
+            if (KIND == EPI_ETD_S1) {
+                float uh, ul;
+                mx::d2ff(uv[j], uh, ul);
+                split_parts<F>(mx::dg32(e.g, uh + ul, alphaf * yv[j], t0f, t1f, i0 + j), 0.f, parts[j]);
+            }
+            if (KIND == EPI_EE || KIND == EPI_ETD_S2 || KIND == EPI_LAWSON2) bad |= !mx::finite_bits(out[j]);
+        }
+        double* dst = (KIND == EPI_STORE) ? e.C : (KIND == EPI_ETD_S1 || KIND == EPI_ETD_S1_NOG) ? e.U2 : e.U;
+        ((double2*)dst)[2 * g] = make_double2(out[0], out[1]);
+        ((double2*)dst)[2 * g + 1] = make_double2(out[2], out[3]);
+        if (KIND == EPI_ETD_S1) {
+            if (flat) {
+#pragma unroll
+                for (int q = 0; q < F::kAParts; ++q) {
+                    if (F::kElem == 4) {
+                        ((uint4*)((uint32_t*)e.W2p + q * e.w2_pitch))[g] =
+                            make_uint4(parts[0][q], parts[1][q], parts[2][q], parts[3][q]);
+                    } else {
+                        ((uint2*)((uint16_t*)e.W2p + q * e.w2_pitch))[g] =
+                            make_uint2(parts[0][q] | (parts[1][q] << 16), parts[2][q] | (parts[3][q] << 16));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t pos = mode1_pos(i0 + j, e.w2_n, e.w2_p, N);
+#pragma unroll
+                    for (int q = 0; q < F::kAParts; ++q) ((PT*)e.W2p)[q * e.w2_pitch + pos] = (PT)parts[j][q];
+                }
+            }
+        }
+    }
+    if (bad && e.status) atomicOr(e.status, MM_STATUS_NONFINITE);
+}
+
+template <class F>
+int launch_update4(const float* y, const Epi& e, int64_t N, cudaStream_t s) {
+    const unsigned grid = (unsigned)std::min<int64_t>((N / 4 + 255) / 256, (int64_t)num_sms() * 8);
+    const float af = (float)e.alpha, t0f = (float)e.t0, t1f = (float)e.t1;
+    switch (e.kind) {
+    case EPI_STORE: update4_kernel<F, EPI_STORE><<<grid, 256, 0, s>>>(y, e, N, af, t0f, t1f); break;
+    case EPI_EE: update4_kernel<F, EPI_EE><<<grid, 256, 0, s>>>(y, e, N, af, t0f, t1f); break;
+    case EPI_ETD_S1: update4_kernel<F, EPI_ETD_S1><<<grid, 256, 0, s>>>(y, e, N, af, t0f, t1f); break;
+    case EPI_ETD_S1_NOG: update4_kernel<F, EPI_ETD_S1_NOG><<<grid, 256, 0, s>>>(y, e, N, af, t0f, t1f); break;
+    case EPI_ETD_S2: update4_kernel<F, EPI_ETD_S2><<<grid, 256, 0, s>>>(y, e, N, af, t0f, t1f); break;
+    case EPI_LAWSON2: update4_kernel<F, EPI_LAWSON2><<<grid, 256, 0, s>>>(y, e, N, af, t0f, t1f); break;
+    default: return MM_ERR_ARG;
+    }
+    MM_LAUNCH_CHECK();
+    return MM_OK;
+}
+
+// Whether the vector epilogue applies: N a multiple of 4, every array it touches
+// 16-byte aligned (and the stage-2 part arrays' pitch a multiple of 4 elements).
+bool update4_ok(const float* y, const Epi& e, int64_t N) {
+    auto al = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
+    if (N % 4 || !al(y) || !al(e.U) || !al(e.U2) || !al(e.C) || !al(e.W2p)) return false;
+    if (e.kind == EPI_ETD_S1 && (e.w2_pitch % 4)) return false;
+    return e.kind != EPI_STORE || (e.D1 == nullptr && e.D2 == nullptr && e.D3 == nullptr);
 }
 
 __global__ void __launch_bounds__(256) split_input_kernel(const double* __restrict__ V, uint8_t* parts,
@@ -246,6 +345,8 @@ int mixed_tucker(mm_plan_s* p, int ell, uint8_t* in_parts, uint8_t* P1, uint8_t*
     Epi last = last0;
     last.prec = p->prec;
     TraceScope tr(KC_SPLIT, s);
+    if (update4_ok(y, last, p->N))
+        return p->prec == MM_BF16X3 ? launch_update4<FormBF16>(y, last, p->N, s) : launch_update4<FormTF32>(y, last, p->N, s);
     mixed_update_kernel<<<(unsigned)grid_of(p->N), 256, 0, s>>>(y, last, p->N, (float)last.alpha,
                                                                  (float)last.t0, (float)last.t1);
     MM_LAUNCH_CHECK();

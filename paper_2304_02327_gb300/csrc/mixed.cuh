@@ -29,9 +29,9 @@ __device__ __forceinline__ double f2d(float f) {
 // x ~ hi + lo with hi = x truncated to 24 significant bits and lo = the next 23
 // bits (|x - hi - lo| <= 2^-46 |x|), from the bits of x, without FP64 arithmetic.
 // |x| < 2^-103 gives lo = 0; |x| < 2^-126 gives hi = lo = 0; inf/nan map to inf/nan.
-__device__ __forceinline__ void d2ff(double x, float& hi, float& lo) {
+__device__ __forceinline__ void d2ff_general(double x, float& hi, float& lo) {
     // branch-free: every case is computed and the right one selected, so a warp never
-    // diverges on the exponent and the elementwise kernels issue no branch here
+    // diverges on the exponent
     const uint64_t b = (uint64_t)__double_as_longlong(x);
     const uint32_t s = (uint32_t)(b >> 63) << 31;
     const int e = (int)((b >> 52) & 0x7ff);
@@ -49,6 +49,29 @@ __device__ __forceinline__ void d2ff(double x, float& hi, float& lo) {
     const float P = __uint_as_float((E0 << 23) | r);
     const float Q = __uint_as_float(E0 << 23);
     lo = __uint_as_float((ef >= 24 && ef < 255) ? (__float_as_uint(P - Q) | s) : 0u);
+}
+
+// The same split with a short path for the values the state holds in practice
+// (2^-103 <= |x| < 2^128, where both parts are FP32 normals, and zero), bit for bit
+// the general split's result there: hi is the sign and the exponent rebased by
+// 896 with the top 23 mantissa bits shifted in (one funnel shift), lo is P - Q as
+// above with P's exponent taken from hi.  Anything else takes d2ff_general.
+__device__ __forceinline__ void d2ff(double x, float& hi, float& lo) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t h = (uint32_t)(b >> 32), l = (uint32_t)b;
+    const uint32_t e = (h >> 20) & 0x7ffu;
+    const uint32_t sg = h & 0x80000000u;
+    const bool zero = ((h & 0x7fffffffu) | l) == 0u;
+    if (e - 920u <= 230u || zero) {
+        const uint32_t hb = __funnelshift_l(l, h - (896u << 20), 3) | sg;
+        const uint32_t qb = (hb & 0x7f800000u) - (23u << 23);
+        const float P = __uint_as_float(qb | ((l >> 6) & 0x7fffffu));
+        const float Q = __uint_as_float(qb);
+        hi = __uint_as_float(zero ? sg : hb);
+        lo = __uint_as_float(zero ? 0u : (__float_as_uint(P - Q) | sg));
+    } else {
+        d2ff_general(x, hi, lo);
+    }
 }
 
 // Round-to-nearest (ties away) FP32 -> TF32, kept in an FP32 container.

@@ -17,6 +17,7 @@
 #include "mixed.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace mm {
 
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(256) stencil2d_kernel(StencilArgsMixed a) {
 
 constexpr int kT2 = 32;      // i_2 extent of a 3D tile
 constexpr int kZ = 32;       // most planes per block of the 3D march
-constexpr int kHalo3 = (kT2 + 2) * (kT1 + 2);      // 612 values of a plane with its halo
+constexpr int kHalo3 = (kT2 + 2) * (kT1 + 2);      // 1156 values of a plane with its halo
 constexpr int kPer3 = (kHalo3 + 255) / 256;         // of them per thread
 
 // The coefficient of the missing neighbour at a grid edge is exactly zero and the
@@ -289,6 +290,142 @@ __global__ void __launch_bounds__(256, 4) stencil3d_kernel(StencilArgsMixed a, i
     }
 }
 
+// The 3D K u + g prepass with the fewest instructions per element (no Riccati or
+// dense terms: d = 3 has neither; N < 2^31, so 32-bit offsets).  The same
+// arithmetic as stencil3d_kernel: g, the row sums times u and the six differences
+// of the double-float split, in FP32, then the form's split of the result.  It
+// marches a 32 x 32 tile of (i_1, i_2) along i_3 with two shared-memory planes:
+// plane z (with its halo) supplies the in-plane neighbours, the centres of planes
+// z - 1 and z + 1 live in registers (the z + 1 centre is read once from the next
+// plane's buffer and then rotated), and the next plane's loads are in flight while
+// plane z is computed.  Templated on the form and on the manufactured g (which
+// needs the element's offset), so no per-element branch on either remains.
+constexpr int kRows3 = kT2 / 8;                      // outputs per thread and plane
+
+// Work balance: the (tile, plane) steps, tile-major, are cut into gridDim.x equal
+// contiguous ranges, one per block of a grid sized to the resident blocks, so every
+// SM marches the same number of planes (a range that crosses a tile boundary
+// restarts the march there).
+template <class F, bool MANUF>
+__global__ void __launch_bounds__(256, 3) stencil3d_reg_kernel(StencilArgsMixed a) {
+    __shared__ float2 sp[2][kT2 + 2][kT1 + 2];
+    using T = typename std::conditional<F::kElem == 4, uint32_t, uint16_t>::type;
+    const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = (int)a.n[2];
+    const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT2 - 1) / kT2;
+    const uint32_t plane = (uint32_t)n1 * (uint32_t)n2;
+    const uint32_t pplane = (uint32_t)a.p1 * (uint32_t)n2;       // one plane in the mode-1 layout
+    const uint32_t pp = (uint32_t)a.part_pitch;
+    const float* cf1 = a.coef[0];
+    const float* cf2 = a.coef[1];
+    const float* cf3 = a.coef[2];
+    const int c = threadIdx.x % kT1, ty = threadIdx.x / kT1;
+    const int64_t total = (int64_t)t1 * t2 * n3;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t s_end = min(total, (int64_t)(blockIdx.x + 1) * per);
+    for (int64_t s0 = (int64_t)blockIdx.x * per; s0 < s_end;) {
+        const int T0 = (int)(s0 / n3);
+        const int a1 = (T0 % t1) * kT1, a2 = (T0 / t1) * kT2, z0 = (int)(s0 % n3);
+        const int z1 = (int)min((int64_t)n3, z0 + (s_end - s0));
+        s0 += z1 - z0;
+        // this thread's share of a plane's halo region
+        uint32_t goff[kPer3];
+        bool gin[kPer3];
+#pragma unroll
+        for (int k = 0; k < kPer3; ++k) {
+            const int e = threadIdx.x + 256 * k;
+            const int r = e / (kT1 + 2), cc = e % (kT1 + 2);
+            const int i1 = a1 - 1 + cc, i2 = a2 - 1 + r;
+            gin[k] = e < kHalo3 && i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2;
+            goff[k] = gin[k] ? (uint32_t)i1 + (uint32_t)n1 * (uint32_t)i2 : 0u;
+        }
+        double raw[kPer3];
+        auto fetch = [&](int z) {           // global loads of plane z, left in flight
+            const bool zin = z >= 0 && z < n3;
+            const double* Uz = a.U + (zin ? plane * (uint32_t)z : 0u);
+#pragma unroll
+            for (int k = 0; k < kPer3; ++k) raw[k] = (gin[k] && zin) ? __ldg(Uz + goff[k]) : 0.0;
+        };
+        auto deposit = [&](int buf) {       // split them into plane buffer buf
+            float2* dst = &sp[buf][0][0];
+#pragma unroll
+            for (int k = 0; k < kPer3; ++k) {
+                const int e = threadIdx.x + 256 * k;
+                if (e < kHalo3) {
+                    float2 v;
+                    mx::d2ff(raw[k], v.x, v.y);
+                    dst[e] = v;
+                }
+            }
+        };
+        // coefficients along i_1 and i_2 are fixed for this thread's outputs
+        const int i1 = a1 + c;
+        const bool in1 = i1 < n1;
+        const float a1a = in1 ? __ldg(cf1 + i1) : 0.f, a1c = in1 ? __ldg(cf1 + n1 + i1) : 0.f;
+        const float a1s = in1 ? __ldg(cf1 + 2 * n1 + i1) : 0.f;
+        float a2a[kRows3], a2c[kRows3], s12[kRows3];
+#pragma unroll
+        for (int q = 0; q < kRows3; ++q) {
+            const int i2 = a2 + ty + 8 * q;
+            const bool in2 = i2 < n2;
+            a2a[q] = in2 ? __ldg(cf2 + i2) : 0.f;
+            a2c[q] = in2 ? __ldg(cf2 + n2 + i2) : 0.f;
+            s12[q] = a1s + (in2 ? __ldg(cf2 + 2 * n2 + i2) : 0.f);
+        }
+        // centres of planes z - 1 (cm) and z (c0) of this thread's outputs
+        float2 cm[kRows3], c0[kRows3];
+        fetch(z0 - 1);
+        deposit((z0 + 1) & 1);
+        fetch(z0);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kRows3; ++q) cm[q] = sp[(z0 + 1) & 1][ty + 8 * q + 1][c + 1];
+        deposit(z0 & 1);
+        fetch(z0 + 1);
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kRows3; ++q) c0[q] = sp[z0 & 1][ty + 8 * q + 1][c + 1];
+        for (int z = z0; z < z1; ++z) {
+            const int b = z & 1, bn = b ^ 1;
+            deposit(bn);                    // plane z + 1 (its buffer held z - 1, read)
+            fetch(z + 2);                   // in flight during this plane's stencil
+            __syncthreads();
+            const float a3a = __ldg(cf3 + z), a3c = __ldg(cf3 + n3 + z), a3s = __ldg(cf3 + 2 * n3 + z);
+            uint32_t pos = (uint32_t)i1 + (uint32_t)a.p1 * (uint32_t)(a2 + ty) + pplane * (uint32_t)z;
+#pragma unroll
+            for (int q = 0; q < kRows3; ++q, pos += 8u * (uint32_t)a.p1) {
+                const int r = ty + 8 * q;
+                const float2 cp = sp[bn][r + 1][c + 1];
+                const float uh = c0[q].x, ul = c0[q].y;
+                const float u = uh + ul;
+                if (in1 && a2 + r < n2) {
+                    float acc;
+                    if (MANUF) {
+                        acc = mx::g32(a.g, u, a.t, (int64_t)i1 + (int64_t)n1 * (a2 + r) + (int64_t)plane * z);
+                    } else {
+                        acc = fmaf(fmaf(fmaf(a.g.f3, u, a.g.f2), u, a.g.f1), u, a.g.f0);
+                    }
+                    acc = fmaf(s12[q] + a3s, u, acc);
+                    acc = stencil_term(a1a, sp[b][r + 1][c], uh, ul, acc);
+                    acc = stencil_term(a1c, sp[b][r + 1][c + 2], uh, ul, acc);
+                    acc = stencil_term(a2a[q], sp[b][r][c + 1], uh, ul, acc);
+                    acc = stencil_term(a2c[q], sp[b][r + 2][c + 1], uh, ul, acc);
+                    acc = stencil_term(a3a, cm[q], uh, ul, acc);
+                    acc = stencil_term(a3c, cp, uh, ul, acc);
+                    uint32_t v[3];
+                    split_parts<F>(acc, 0.f, v);
+                    T* w = (T*)a.Wp + pos;
+                    w[0] = (T)v[0];
+                    w[pp] = (T)v[1];
+                    if (F::kAParts == 3) w[2 * pp] = (T)v[2];
+                }
+                cm[q] = c0[q];
+                c0[q] = cp;
+            }
+            __syncthreads();                // before the next deposit overwrites plane z
+        }
+    }
+}
+
 __global__ void stencil_coef_kernel(const double* __restrict__ A, int n, float* coef) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double a = i > 0 ? A[i + (int64_t)n * (i - 1)] : 0.0;
@@ -322,7 +459,21 @@ int launch_prepass_mixed(const StencilArgsMixed& a0, float2* Up, cudaStream_t s)
         const unsigned grid = (unsigned)std::min<int64_t>(tiles, target);
         TraceScope tr(KC_PREPASS, s);
         if (a.d == 2) stencil2d_kernel<<<grid, 256, 0, s>>>(a);
-        else stencil3d_kernel<<<grid, 256, 0, s>>>(a, zc);
+        else if (!a.yadd && !a.yadd2 && !a.cadd && a.N < (int64_t(1) << 31) &&
+                 (int64_t)a.part_pitch * (a.prec == MM_BF16X3 ? 3 : 2) < (int64_t(1) << 31)) {
+            const bool manuf = a.g.kind == MM_G_ADR_MANUFACTURED;
+            auto kern = a.prec == MM_BF16X3 ? (manuf ? stencil3d_reg_kernel<FormBF16, true>
+                                                     : stencil3d_reg_kernel<FormBF16, false>)
+                                            : (manuf ? stencil3d_reg_kernel<FormTF32, true>
+                                                     : stencil3d_reg_kernel<FormTF32, false>);
+            int per_sm = 0;
+            MM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+            const int64_t steps = ((a.n[0] + kT1 - 1) / kT1) * ((a.n[1] + kT2 - 1) / kT2) * a.n[2];
+            const unsigned g3 = (unsigned)std::max<int64_t>(1, std::min<int64_t>(steps, (int64_t)num_sms() * std::max(per_sm, 1)));
+            kern<<<g3, 256, 0, s>>>(a);
+        } else {
+            stencil3d_kernel<<<grid, 256, 0, s>>>(a, zc);
+        }
         MM_LAUNCH_CHECK();
         return MM_OK;
     }
