@@ -56,6 +56,12 @@ from paper_2304_02327_gb300 import parallel, workloads as wl  # noqa: E402
 METRIC = "DOF-steps/s"
 DEFAULT_WORKLOAD = "adr3d_n320_etd2rk"
 DEFAULT_BATCH = "batch_ac2d_1024_expeuler"
+# The other measured configurations, recorded beside the headline in every form:
+# 2D Allen-Cahn n = 64 (exp. Euler), 3D ADR n = 128 (ETD2RK), matrix Riccati
+# n = 2048 (exp. Euler and ETD2RK).
+OTHER_CONFIGS = ("ac2d_n64_expeuler", "adr3d_n128_etd2rk", "riccati_n2048_expeuler", "riccati_n2048_etd2rk")
+# whose whole run the oracle finishes in seconds on the host cores
+ORACLE_WHOLE_RUN = ("ac2d_n64_expeuler", "adr3d_n128_etd2rk")
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2, written between timed steps
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk x 2.07 GHz
 CUBLAS_DGEMM_TFLOPS_MEASURED = 1.10          # torch.matmul float64 8192^3 on this pool
@@ -88,6 +94,8 @@ def parse():
     ap.add_argument("--batch", default=DEFAULT_BATCH,
                     help="batched workload recorded beside the headline ('none' to skip)")
     ap.add_argument("--batch-prec", default="bf16x3", choices=["tf32x3", "bf16x3"])
+    ap.add_argument("--configs", default="all",
+                    help="record the other configurations too ('all' or 'none')")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the error records (full run vs FP64, sampled step vs oracle)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -433,6 +441,48 @@ def accuracy_single(api, p, forms, nsample=24):
     return out, sample
 
 
+def other_config(api, name, forms, args, flush, stream, world, local, rank):
+    """One further configuration in every form: throughput (the same timing as the
+    headline, fewer steps, no e2e), the contraction's roofline fraction, and the
+    errors: each split-precision run against the FP64 GPU run, the FP64 last step
+    against the oracle on sampled entries, and for the small configurations the
+    whole FP64 run against the oracle's."""
+    import copy
+    p = wl.workload(name)
+    p.name_tag = name
+    a = copy.copy(args)
+    a.steps, a.warmup = min(args.steps, 10), min(args.warmup, 3)
+    rec = {"N": p.N, "n": p.n, "scheme": wl.SCHEME_NAMES[p.scheme], "steps_of_workload": p.steps, "forms": {}}
+    for prec in ["fp64"] + [f for f in forms if f != "fp64"]:
+        r = time_single(api, p, prec, a, flush, stream, world, local, do_e2e=False)
+        rf = r["roofline"]
+        rec["forms"][prec] = {"value": r["value"], "unit": METRIC, "ms_per_step": r["ms_per_step"],
+                              "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                              "avg_launch_ms", "share_of_step_time")},
+                              "kernel_ms_per_step": r["kernel_ms_per_step"], "gpu_launches": r["gpu_launches"],
+                              "clocks": r["clocks"]}
+    fp = rec["forms"]["fp64"]["ms_per_step"]
+    for prec, r in rec["forms"].items():
+        r["speedup_vs_fp64"] = fp / r["ms_per_step"]
+    if rank == 0 and not args.no_accuracy:
+        errs, sample = accuracy_single(api, p, ["fp64"] + forms, nsample=24 if p.d == 3 else 64)
+        for prec, e in errs.items():
+            rec["forms"][prec]["rel_err"] = e
+        rec["rel_err_sample"] = sample
+        if name in ORACLE_WHOLE_RUN:
+            import torch
+            from oracle.integrators import OracleProblem, integrate, rel_err_fro, rel_err_inf
+            ref = integrate(OracleProblem.from_problem(p), p.u0, p.scheme, p.steps)
+            plan, g, U = api.setup(p, "fp64")
+            api.expint_step(plan, p.scheme, U, p.steps, g=g)
+            torch.cuda.synchronize()
+            got = U.cpu().numpy()
+            rec["forms"]["fp64"]["rel_err"]["whole_run_vs_oracle"] = {
+                "steps": p.steps, "inf": rel_err_inf(got, ref), "fro": rel_err_fro(got, ref)}
+            del plan, g, U
+    return rec
+
+
 def run_oracle_sample(problem, seconds):
     """The FP64 oracle as it stands on a bounded number of steps from u0."""
     from oracle.integrators import OracleProblem, step
@@ -506,21 +556,21 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
     value = parallel.job_throughput([dof_all * args.steps], t_ms / 1e3)
     ms_step = t_ms / args.steps
 
-    # ---- per-kernel device times: the same launches, eager and traced ----
-    bp = api.Batch(plans, gs, Us, autotune=False, nc_cap=b.info()["nc_cap"], graph=False)
-    bp.run(1)
+    # ---- per-kernel device times: the same batch's launches, eager and traced ----
+    b.set_graph(False)
+    b.run(1)
     torch.cuda.synchronize()
     api.trace_enable(True)
     ksteps = min(args.steps, 5)
     for k in range(ksteps):
         flush.fill_(k & 0xff)
-        bp.run(1)
+        b.run(1)
     torch.cuda.synchronize()
     n_launch, k_ms = api.trace_read(api.KC_CONTRACT_TF32)
     _, pre_ms = api.trace_read(api.KC_PREPASS)
     _, upd_ms = api.trace_read(api.KC_SPLIT)
     api.trace_enable(False)
-    bp.close()
+    b.set_graph(True)
 
     # ---- e2e: every state in from pinned host memory, one step, every state out ----
     hosts = [torch.from_numpy(np.ascontiguousarray(p.u0)).pin_memory() for p in probs]
@@ -571,6 +621,7 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
     del fp_plans, fp_gs, fp_Us, fp_ws
 
     info = b.info()
+    sched = b.schedule()
     b.close()
     del plans, gs, Us
     torch.cuda.empty_cache()
@@ -589,6 +640,11 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
            "sizes": "n uniform over {48, 64, ..., 512}, square", "scheme": "expeuler",
            "tau": probs_all[0].tau, "size_classes": info["classes"],
            ("nc_cap_pinned" if args.nc_cap else "nc_cap_autotuned"): info["nc_cap"],
+           "autotuned_schedule": None if args.nc_cap else {
+               "widths_by_class": sched["widths"], "per_class_widths_kept": sched["per_class"],
+               "tucker_ms_uniform_width": sched["tucker_ms_uniform"],
+               "tucker_ms_chosen": sched["tucker_ms_chosen"],
+               "tile_order": "decreasing cost, taken round-robin by one CTA per SM"},
            "tiles_per_mode": info["tiles_mode1"],
            "plan_ms": plan_ms, "batch_create_ms": create_ms,
            "graph": "one CUDA graph launch per step",
@@ -761,6 +817,11 @@ def ours(args):
     if args.batch and args.batch != "none":
         batched = time_batched(api, args.batch, args.batch_prec, args, flush, stream, world, local, rank,
                                do_check=not args.no_accuracy)
+    others = {}
+    if args.configs != "none":
+        for name in OTHER_CONFIGS:
+            if name != args.workload:
+                others[name] = other_config(api, name, forms, args, flush, stream, world, local, rank)
 
     if rank != 0:
         if world > 1:
@@ -792,6 +853,8 @@ def ours(args):
         line["mixed"] = mixed
     if batched is not None:
         line["batched"] = batched
+    if others:
+        line["other_configs"] = others
 
     if not args.no_accuracy:
         errs, sample = accuracy_single(api, p, [args.prec] + forms)

@@ -267,9 +267,12 @@ MM_API int tucker_apply_noalloc(int d, const int64_t* n, const double* const* M,
  * K u + g prepass, one persistent tensor-core launch per direction over the tiles
  * of every instance, the FP64 update), captured once in a CUDA graph.
  *
- * mm_tune: autotune = 1 times the candidate tile widths nc in {160, 128, 96, 64} on
- * the batch's own Tucker launches at creation and keeps the fastest; nc_cap = 16..160
- * (a multiple of 16) fixes the width instead (0: autotune or 160); graph = 1 makes
+ * mm_tune: autotune = 1 picks the tile widths at creation by timing the batch's own
+ * Tucker launches: every candidate nc in {160, 128, 96, 64} for all size classes at
+ * once, then each class alone at every candidate, and keeps the per-class choices
+ * if they beat the best uniform width (expint_batch_schedule reports the result);
+ * nc_cap = 16..160 (a multiple of 16) fixes the width instead (0: autotune or 160);
+ * graph = 1 makes
  * expint_batch_run replay a captured graph of its nsteps steps (0: plain launches).
  * A NULL mm_tune means {autotune 0, nc_cap 0, graph 1}. */
 typedef struct mm_tune {
@@ -308,10 +311,24 @@ MM_API int expint_batch_run(mm_batch b, double t0, int nsteps, void* stream);
 /* Synchronises `stream`; OR of MM_STATUS_* raised by the batch (>= 0). */
 MM_API int expint_batch_status(mm_batch b, int reset, void* stream);
 
-/* Host query: number of size classes, the tile width in use, mode-1 tiles per
- * step, total degrees of freedom.  Any pointer may be NULL. */
+/* Host query: number of size classes, the tile width of class 0 (of every class
+ * unless the autotuner kept per-class widths), mode-1 tiles per step, total degrees
+ * of freedom.  Any pointer may be NULL. */
 MM_API int expint_batch_info(mm_batch b, int* nclasses, int* nc_cap, int64_t* tiles_mode1,
                              int64_t* total_dof);
+
+/* Host query of the autotuner's outcome: the tile width of every size class (into
+ * nc_per_class, max_classes entries, or NULL), the number of classes, and the Tucker
+ * time of one step (both directions, ms) with the best uniform width and with the
+ * widths in use (0 without autotuning).  Returns 1 if per-class widths were kept,
+ * 0 if one width serves every class, or MM_ERR_ARG (b NULL, max_classes too small). */
+MM_API int expint_batch_schedule(mm_batch b, int32_t* nc_per_class, int max_classes, int* nclasses,
+                                 float* ms_uniform, float* ms_chosen);
+
+/* Host setting: expint_batch_run replays a captured graph (on != 0, the default of
+ * mm_tune) or launches the kernels directly (on = 0: each launch then carries its
+ * own trace events, see mm_trace_enable).  Errors: MM_ERR_ARG. */
+MM_API int expint_batch_set_graph(mm_batch b, int on);
 
 /* Frees the batch (synchronises the device).  NULL is OK. */
 MM_API int expint_batch_destroy(mm_batch b);

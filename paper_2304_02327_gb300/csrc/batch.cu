@@ -198,6 +198,9 @@ struct mm_batch_s {
     std::vector<Cls> cls;
     std::vector<TcClassSpec> spec1, spec2;   // per class, mode 1 and mode 2
     std::vector<int> nc_cap;                 // per class (same for both modes)
+    float tune_ms_uniform = 0.f;             // autotuner: best uniform width's Tucker time
+    float tune_ms_chosen = 0.f;              //   and the time of the widths kept
+    int tune_per_class = 0;                  //   1: the per-class widths won
     struct Launch {                          // groups of <= MM_TC_MAX_CLASSES classes
         int c0, nc;
         int4* tiles1 = nullptr;
@@ -285,31 +288,90 @@ int one_step(mm_batch_s* b, double t, cudaStream_t s) {
     return MM_OK;
 }
 
-// Try every candidate tile width on the batch's own Tucker launches (they touch
-// only the workspace) and keep the fastest.
+// Mean time of `reps` runs of fn after one warm-up run, in ms.
+template <class Fn>
+int time_ms(Fn fn, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* ms, int reps = 3) {
+    int rc = fn();
+    if (rc) return rc;
+    MM_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps && !rc; ++r) rc = fn();
+    if (rc) return rc;
+    MM_CUDA_TRY(cudaEventRecord(e1, s));
+    MM_CUDA_TRY(cudaEventSynchronize(e1));
+    MM_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= reps;
+    return MM_OK;
+}
+
+// Both directions of class c alone at width nc: its tiles go into its launch
+// group's tile arrays (sized for the narrowest width of every class in the group).
+int time_class(mm_batch_s* b, int c, int nc, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+    const mm_batch_s::Launch* L = nullptr;
+    for (auto& G : b->launches)
+        if (c >= G.c0 && c < G.c0 + G.nc) L = &G;
+    if (!L) return MM_ERR_ARG;
+    std::vector<int4> t1, t2;
+    int rc = tc_group_tiles(b->prec, &b->spec1[c], 1, &nc, t1);
+    if (!rc) rc = tc_group_tiles(b->prec, &b->spec2[c], 1, &nc, t2);
+    if (rc) return rc;
+    if ((int64_t)t1.size() > L->cap1 || (int64_t)t2.size() > L->cap2) return MM_ERR_ARG;
+    MM_CUDA_TRY(cudaMemcpyAsync(L->tiles1, t1.data(), t1.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    MM_CUDA_TRY(cudaMemcpyAsync(L->tiles2, t2.data(), t2.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    MM_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t n1 = (int64_t)t1.size(), n2 = (int64_t)t2.size();
+    return time_ms([&] {
+        int r = tc_group_product(b->prec, &b->spec1[c], 1, &nc, L->tiles1, n1, b->status, s);
+        return r ? r : tc_group_product(b->prec, &b->spec2[c], 1, &nc, L->tiles2, n2, b->status, s);
+    }, s, e0, e1, ms);
+}
+
+// The autotuner, on the batch's own Tucker launches (they touch only the
+// workspace):
+//   1. every candidate width for all classes at once; the fastest is the uniform choice;
+//   2. each class alone at every candidate width (a size class's best width depends
+//      on its n: how its columns split into tiles and how many tiles it brings);
+//   3. the per-class choices together, kept only if faster than the uniform one.
+// Tiles within a launch are always ordered by decreasing cost (the CTAs take them
+// round-robin).  The times of both schedules are kept for expint_batch_schedule.
 int autotune(mm_batch_s* b, cudaStream_t s) {
     cudaEvent_t e0, e1;
     MM_CUDA_TRY(cudaEventCreate(&e0));
-    MM_CUDA_TRY(cudaEventCreate(&e1));
-    int best = -1;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return MM_ERR_CUDA;
+    }
+    const int ncls = (int)b->cls.size();
+    auto all_modes = [&] { return tucker_modes(b, s); };
+    int rc = MM_OK, best = -1;
     float best_ms = 0.f;
-    int rc = MM_OK;
     for (int cand : kNcCandidates) {
         for (auto& v : b->nc_cap) v = cand;
-        if ((rc = build_tiles(b, s))) break;
-        if ((rc = tucker_modes(b, s))) break;            // warm-up
-        if (cudaEventRecord(e0, s) != cudaSuccess) { rc = MM_ERR_CUDA; break; }
-        for (int r = 0; r < 3 && !rc; ++r) rc = tucker_modes(b, s);
-        if (rc) break;
         float ms = 0.f;
-        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) { rc = MM_ERR_CUDA; break; }
+        if ((rc = build_tiles(b, s)) || (rc = time_ms(all_modes, s, e0, e1, &ms))) break;
         if (best < 0 || ms < best_ms) { best = cand; best_ms = ms; }
+    }
+    std::vector<int> per(ncls, best);
+    for (int c = 0; c < ncls && !rc; ++c) {
+        float cbest = -1.f;
+        for (int cand : kNcCandidates) {
+            float ms = 0.f;
+            if ((rc = time_class(b, c, cand, s, e0, e1, &ms))) break;
+            if (cbest < 0.f || ms < cbest) { cbest = ms; per[c] = cand; }
+        }
+    }
+    float per_ms = 0.f;
+    if (!rc) {
+        b->nc_cap = per;
+        if (!(rc = build_tiles(b, s))) rc = time_ms(all_modes, s, e0, e1, &per_ms);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    for (auto& v : b->nc_cap) v = best;
+    b->tune_ms_uniform = best_ms;
+    b->tune_per_class = per_ms < best_ms;
+    b->tune_ms_chosen = b->tune_per_class ? per_ms : best_ms;
+    if (!b->tune_per_class)
+        for (auto& v : b->nc_cap) v = best;
     return build_tiles(b, s);
 }
 
@@ -621,6 +683,23 @@ extern "C" int expint_batch_info(mm_batch b, int* nclasses, int* nc_cap, int64_t
         *tiles_mode1 = t;
     }
     if (total_dof) *total_dof = b->total_dof;
+    return MM_OK;
+}
+
+extern "C" int expint_batch_schedule(mm_batch b, int32_t* nc_per_class, int max_classes, int* nclasses,
+                                     float* ms_uniform, float* ms_chosen) {
+    if (!b || (nc_per_class && max_classes < (int)b->cls.size())) return MM_ERR_ARG;
+    if (nclasses) *nclasses = (int)b->cls.size();
+    if (nc_per_class)
+        for (size_t c = 0; c < b->cls.size(); ++c) nc_per_class[c] = b->nc_cap[c];
+    if (ms_uniform) *ms_uniform = b->tune_ms_uniform;
+    if (ms_chosen) *ms_chosen = b->tune_ms_chosen;
+    return b->tune_per_class;
+}
+
+extern "C" int expint_batch_set_graph(mm_batch b, int on) {
+    if (!b) return MM_ERR_ARG;
+    b->use_graph = on != 0;
     return MM_OK;
 }
 

@@ -93,9 +93,29 @@ def test_batch_graph_and_plain_launches_agree(api, form):
 
 
 def test_batch_autotune_picks_a_candidate(api, form):
-    probs = small_batch(steps=2)
-    _, b = run_batch(api, probs, form, 2, autotune=True)
+    """The autotuner's schedule: a candidate width per size class, kept per class only
+    when faster than the best uniform width; the tuned batch still reproduces the
+    single-problem path bit for bit (the width never changes an element's products)."""
+    probs = small_batch(steps=3)
+    got, b = run_batch(api, probs, form, 3, autotune=True)
+    sch = b.schedule()
     assert b.info()["nc_cap"] in (160, 128, 96, 64)
+    assert len(sch["widths"]) == b.info()["classes"]
+    assert set(sch["widths"]) <= {160, 128, 96, 64}
+    assert sch["per_class"] or len(set(sch["widths"])) == 1
+    assert 0 < sch["tucker_ms_chosen"] <= sch["tucker_ms_uniform"]
+    for p, g in zip(probs, got):
+        plan, gg, U = api.setup(p, form)
+        api.expint_step(plan, p.scheme, U, 3, g=gg)
+        np.testing.assert_array_equal(g, U.cpu().numpy(), err_msg=p.name)
+    # eager launches of the same tuned batch continue exactly like the graph replays
+    b2 = run_batch(api, probs, form, 3, autotune=False, nc_cap=64)[1]
+    b.set_graph(False)
+    b.run(2)
+    b2.run(2)
+    torch.cuda.synchronize()
+    for a, c in zip(b.Us, b2.Us):
+        assert torch.equal(a, c)
 
 
 def test_batch_rejects_unsupported(api):
