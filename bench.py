@@ -631,8 +631,10 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
     peak, note = tensor_peak(prec)
     achieved = NPROD[prec] * flops_launch / (k_avg / 1e3) / 1e12 if k_avg else None
     E, P = ELEM[prec], PARTS[prec]
-    # mode 1: parts in, parts out; mode 2: parts in, FP32 result out
-    bpl = (P * E * dof + P * E * dof + P * E * dof + 4 * dof) / 2
+    # per launch: the operand's parts in and every instance's phi_1 in three parts
+    # (3 E n^2 = 3 E DOF for square instances); mode 1 writes the next mode's parts,
+    # mode 2 the FP32 result
+    bpl = (P * E * dof + 3 * E * dof + P * E * dof + P * E * dof + 3 * E * dof + 4 * dof) / 2
     hb, hnote = hbm_peak()
     gbs = bpl / (k_avg / 1e3) / 1e9 if k_avg else None
     rec = {"workload": name, "value": value, "unit": METRIC, "ms_per_step": ms_step,
