@@ -36,16 +36,17 @@
 //               operand (the 3-D maps {K, rows, part} zero-fill the ragged K tail
 //               and the last rows)
 //   warp 1      MMA issuer (one thread): per K-block one asm block of main-product
-//               MMAs into the current slot of a two-slot ring (a fresh slot every
-//               kGroup K-blocks) and one of corrections into the tile's accumulator
+//               MMAs into the current slot of a kMainSlots-slot ring (a fresh slot
+//               every kGroup K-blocks) and one of corrections into the tile's
+//               accumulator
 //   warps 2-17  epilogue, four warps per TMEM lane quarter, each owning a quarter
 //               of the columns: drain each main slot into register accumulators as
 //               it completes, then add the corrections and write the next mode's
-//               split operand (or FP32 after the last mode); the two-slot ring lets
-//               the MMAs of the next tile's first K-blocks run meanwhile
-// TMEM: [main slot 0 | main slot 1 | corrections], nc columns each; the next tile's
-// corrections wait until the epilogue has read this tile's.  Every mbarrier wait is
-// bounded (tcgen05.cuh).
+//               split operand (or FP32 after the last mode); the slot ring lets the
+//               MMAs of the next tile's first K-blocks run meanwhile
+// TMEM: [main slot 0 | ... | main slot kMainSlots-1 | corrections], nc columns each;
+// the next tile's corrections wait until the epilogue has read this tile's.  Every
+// mbarrier wait is bounded (tcgen05.cuh).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -74,13 +75,21 @@ constexpr int kMaxStages = 4;
 // contraction time.
 constexpr int kGroup = 1;
 constexpr int kBParts = 3;                 // Phi = b0 + b1 + b2 in both forms
-constexpr int kNcMax = 160;                // [main slot 0 | main slot 1 | corr] fit 512 TMEM columns
-constexpr int kBars = 2 * kMaxStages + 9;  // full, empty per stage; main full/empty (slot);
-                                           // corr full/empty (tile parity); mma_done
+// TMEM main-product slots in the ring.  [main slots | corrections] share the 512 TMEM
+// columns, which caps the tile width: two slots allow tiles of 160 columns.  Measured
+// with three slots (tiles of <= 128 columns, so the next tile's MMAs run three K-blocks
+// ahead of the epilogue's stores): the n = 320 contraction went from 0.636 to 0.780 ms
+// per ETD2RK step (three column splits of 112 instead of two of 160), the batch's from
+// 0.910 to 1.033 ms; only the n = 2048 Riccati products gained (0.905 -> 0.893 ms).
+constexpr int kMainSlots = 2;
+constexpr int kNcMax = 512 / (kMainSlots + 1) / 16 * 16;
+constexpr int kBars = 2 * kMaxStages + 2 * kMainSlots + 5;  // full, empty per stage; main full/empty
+                                                            // per slot; corr full/empty (tile
+                                                            // parity); mma_done
 constexpr int kSmemLimit = 227 * 1024;
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr int kChunks = 3;                 // 16-column chunks per epilogue warp (4 x 3 x 16 >= kNcMax)
+constexpr int kChunks = (kNcMax + 63) / 64;  // 16-column chunks per epilogue warp (4 x kChunks x 16 >= kNcMax)
 constexpr int kQuartCols = 16 * kChunks;   // columns per epilogue thread (upper bound)
 constexpr int kMaxClasses = MM_TC_MAX_CLASSES;
 
@@ -270,10 +279,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
     // the "full" barriers are waited only by the epilogue (in K-block / tile
     // order), the "empty" ones only by the MMA thread.
     auto mfull = [&](int r) { return tc::smem_u32(bars + 2 * kMaxStages + r); };
-    auto mempty = [&](int r) { return tc::smem_u32(bars + 2 * kMaxStages + 2 + r); };
-    auto cfull = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 4 + b); };
-    auto cempty = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 6 + b); };
-    const uint32_t mma_done = tc::smem_u32(bars + 2 * kMaxStages + 8);
+    auto mempty = [&](int r) { return tc::smem_u32(bars + 2 * kMaxStages + kMainSlots + r); };
+    auto cfull = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 2 * kMainSlots + b); };
+    auto cempty = [&](int b) { return tc::smem_u32(bars + 2 * kMaxStages + 2 * kMainSlots + 2 + b); };
+    const uint32_t mma_done = tc::smem_u32(bars + 2 * kMaxStages + 2 * kMainSlots + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int stages = g.stages;
@@ -284,9 +293,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             tc::mbar_init(full(s), 1);
             tc::mbar_init(empty(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kMainSlots; ++b) {
             tc::mbar_init(mfull(b), 1);
             tc::mbar_init(mempty(b), kEpiWarps);
+        }
+        for (int b = 0; b < 2; ++b) {
             tc::mbar_init(cfull(b), 1);
             tc::mbar_init(cempty(b), kEpiWarps);
         }
@@ -343,9 +354,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             int s = 0;                     // stage of the next K-block
             uint32_t ph = 0;               // its fill phase parity
             int64_t git = 0;               // main-slot groups issued
-            int64_t uses[2] = {0, 0};      // uses of each main slot so far
+            int64_t uses[kMainSlots] = {};  // uses of each main slot so far
             bool ok = true;
-            const uint32_t corr = tmem + (uint32_t)(2 * g.stage_nc);   // the tile's corrections
+            const uint32_t corr = tmem + (uint32_t)(kMainSlots * g.stage_nc);   // the tile's corrections
             const uint32_t sbase = tc::smem_u32(smem);
             const uint32_t bstep = b_slot >> 4;                        // one B part, descriptor units
             for (int64_t i = 0; i < my_tiles && ok; ++i) {
@@ -361,7 +372,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                     const bool gfirst = (kb % kGroup) == 0;
                     const bool glast = (kb % kGroup) == kGroup - 1 || kb == k.nkb - 1;
                     if (gfirst) {
-                        r = (int)(git & 1);
+                        r = (int)(git % kMainSlots);
                         if (uses[r] >= 1 && !tc::mbar_wait(mempty(r), (uint32_t)(uses[r] - 1) & 1, g.status)) {
                             ok = false;
                             break;
@@ -410,8 +421,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             // main product, one slot (kGroup stages) at a time, summed in FP32 registers
             const int ngroups = (k.nkb + kGroup - 1) / kGroup;
             for (int gi = 0; gi < ngroups && ok; ++gi, ++it) {
-                const int rs = (int)(it & 1);
-                ok = __all_sync(0xffffffffu, tc::mbar_wait(mfull(rs), (uint32_t)(it >> 1) & 1, g.status));
+                const int rs = (int)(it % kMainSlots);
+                ok = __all_sync(0xffffffffu, tc::mbar_wait(mfull(rs), (uint32_t)(it / kMainSlots) & 1, g.status));
                 if (!ok) break;
                 tc::tc_fence_after();
                 const uint32_t slot = tmem + lane_off + (uint32_t)(rs * g.stage_nc);
@@ -439,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
             // next-mode layout of output (q, i): position jq + p' (rq + (R / n') i)
             int64_t jq = 0, rq = 0;
             if (!k.last) { jq = q % k.next_n; rq = q / k.next_n; }
-            const uint32_t cset = tmem + lane_off + (uint32_t)(2 * g.stage_nc);
+            const uint32_t cset = tmem + lane_off + (uint32_t)(kMainSlots * g.stage_nc);
 #pragma unroll
             for (int c = 0; c < kQuartCols / 16; ++c) {    // y = corrections + main, in FP32
                 if (c0 + c < c1) {
@@ -560,6 +571,7 @@ struct Geometry {
 // Columns per CTA tile given at most nc_cap (a multiple of 16, <= kNcMax): the
 // fewest splits, then the narrowest multiple of 16 that covers the columns.
 Geometry split_cols(int ncols, int nc_cap) {
+    nc_cap = std::min(nc_cap, kNcMax);
     const int n16 = round_up(ncols, 16);
     Geometry g;
     g.splits = (n16 + nc_cap - 1) / nc_cap;
