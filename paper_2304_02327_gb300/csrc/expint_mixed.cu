@@ -395,6 +395,7 @@ int mixed_expint(mm_plan_s* p, int scheme, const mm_nonlin* gd, double* U, doubl
     a.yadd2 = riccati ? w.yq : nullptr;
     a.cadd = riccati ? gd->C : nullptr;
     a.part_pitch = in1.part_pitch; a.p1 = in1.p; a.prec = p->prec;
+    a.status = p->status;
     int64_t st = 1;
     for (int mu = 0; mu < d; ++mu) {
         a.n[mu] = p->n[mu];

@@ -15,6 +15,8 @@
 #include "trace.cuh"
 #include "forms.cuh"
 #include "mixed.cuh"
+#include "tcgen05.cuh"
+#include "tf32.cuh"
 
 #include <algorithm>
 #include <type_traits>
@@ -426,6 +428,159 @@ __global__ void __launch_bounds__(256, 3) stencil3d_reg_kernel(StencilArgsMixed 
     }
 }
 
+// The same march with the planes brought in by TMA: a ring of kTmaStages raw FP64
+// planes (each the 36 x 34 box at (a1 - 2, a2 - 1, z), so that the box starts on a
+// 16-byte boundary; rows and planes outside the array read zeros, which is the
+// Dirichlet halo), filled up to kTmaStages planes ahead by thread 0, so that many
+// loads are in flight per block without holding them in registers; each plane is
+// split once from the ring into the two float2 planes of stencil3d_reg_kernel.  The
+// arithmetic, its order and the work balance are stencil3d_reg_kernel's.  Every wait
+// on a plane is bounded: on timeout the status word gets MM_STATUS_TIMEOUT, the block
+// stops after its next barrier, and thread 0 waits (bounded) for its copies in flight.
+constexpr int kTmaStages = 4;
+constexpr int kRawX = kT1 + 4;                                   // 36 doubles: a1 - 2 .. a1 + 33
+constexpr int kRawY = kT2 + 2;                                   // 34 rows: a2 - 1 .. a2 + 32
+constexpr uint32_t kRawBytes = kRawX * kRawY * 8;                // 9792 bytes per plane
+constexpr uint32_t kRawStride = (kRawBytes + 127) / 128 * 128;
+constexpr uint32_t kSplitBytes = 2 * (kT2 + 2) * (kT1 + 2) * sizeof(float2);
+constexpr size_t kTmaSmem = 128 + kTmaStages * kRawStride + kSplitBytes + kTmaStages * 8;
+
+template <class F, bool MANUF>
+__global__ void __launch_bounds__(256, 3) stencil3d_tma_kernel(const __grid_constant__ CUtensorMap map,
+                                                               StencilArgsMixed a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    float2(*sp)[kT2 + 2][kT1 + 2] = (float2(*)[kT2 + 2][kT1 + 2])(sm + kTmaStages * kRawStride);
+    uint64_t* bars = (uint64_t*)(sm + kTmaStages * kRawStride + kSplitBytes);
+    __shared__ int fail;
+    using T = typename std::conditional<F::kElem == 4, uint32_t, uint16_t>::type;
+    const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = (int)a.n[2];
+    const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT2 - 1) / kT2;
+    const uint32_t plane = (uint32_t)n1 * (uint32_t)n2;
+    const uint32_t pplane = (uint32_t)a.p1 * (uint32_t)n2;
+    const uint32_t pp = (uint32_t)a.part_pitch;
+    const float* cf1 = a.coef[0];
+    const float* cf2 = a.coef[1];
+    const float* cf3 = a.coef[2];
+    const int c = threadIdx.x % kT1, ty = threadIdx.x / kT1;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kTmaStages; ++st) tc::mbar_init(tc::smem_u32(bars + st), 1);
+        tc::fence_mbar_init();
+        fail = 0;
+    }
+    __syncthreads();
+    int64_t issued = 0, consumed = 0;    // planes loaded / taken from the ring by this block
+    const int64_t total = (int64_t)t1 * t2 * n3;
+    const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const int64_t s_end = min(total, (int64_t)(blockIdx.x + 1) * per);
+    for (int64_t s0 = (int64_t)blockIdx.x * per; s0 < s_end;) {
+        const int T0 = (int)(s0 / n3);
+        const int a1 = (T0 % t1) * kT1, a2 = (T0 / t1) * kT2, z0 = (int)(s0 % n3);
+        const int z1 = (int)min((int64_t)n3, z0 + (s_end - s0));
+        s0 += z1 - z0;
+        // planes z0 - 1 .. z1 of this segment, loaded in order into the ring
+        const int64_t first = issued, nplanes = z1 - z0 + 2;
+        auto issue = [&](int64_t k) {        // thread 0: plane z0 - 1 + (k - first)
+            const int st = (int)(k % kTmaStages);
+            const uint32_t bar = tc::smem_u32(bars + st);
+            tc::mbar_arrive_expect_tx(bar, kRawBytes);
+            tc::tma_load_3d(tc::smem_u32(sm + st * kRawStride), &map, a1 - 2, a2 - 1, z0 - 1 + (int)(k - first), bar);
+        };
+        if (threadIdx.x == 0) {
+            tc::fence_proxy_async_smem();
+            for (; issued < first + min((int64_t)kTmaStages, nplanes); ++issued) issue(issued);
+        }
+        // take the next plane from the ring and split it into float2 plane buf
+        auto take = [&](int buf) -> bool {
+            const int st = (int)(consumed % kTmaStages);
+            if (!tc::mbar_wait(tc::smem_u32(bars + st), (uint32_t)(consumed / kTmaStages) & 1, a.status)) fail = 1;
+            const double* rp = (const double*)(sm + st * kRawStride);
+            float2* dst = &sp[buf][0][0];
+#pragma unroll
+            for (int k = 0; k < kPer3; ++k) {
+                const int e = threadIdx.x + 256 * k;
+                if (e < kHalo3) {
+                    const int r = e / (kT1 + 2), cc = e % (kT1 + 2);
+                    float2 v;
+                    mx::d2ff(rp[r * kRawX + cc + 1], v.x, v.y);
+                    dst[e] = v;
+                }
+            }
+            ++consumed;
+            __syncthreads();
+            if (threadIdx.x == 0 && issued < first + nplanes && !fail) {   // refill the stage just read
+                tc::fence_proxy_async_smem();
+                issue(issued++);
+            }
+            return fail == 0;
+        };
+        const int i1 = a1 + c;
+        const bool in1 = i1 < n1;
+        const float a1a = in1 ? __ldg(cf1 + i1) : 0.f, a1c = in1 ? __ldg(cf1 + n1 + i1) : 0.f;
+        const float a1s = in1 ? __ldg(cf1 + 2 * n1 + i1) : 0.f;
+        float a2a[kRows3], a2c[kRows3], s12[kRows3];
+#pragma unroll
+        for (int q = 0; q < kRows3; ++q) {
+            const int i2 = a2 + ty + 8 * q;
+            const bool in2 = i2 < n2;
+            a2a[q] = in2 ? __ldg(cf2 + i2) : 0.f;
+            a2c[q] = in2 ? __ldg(cf2 + n2 + i2) : 0.f;
+            s12[q] = a1s + (in2 ? __ldg(cf2 + 2 * n2 + i2) : 0.f);
+        }
+        float2 cm[kRows3], c0[kRows3];
+        if (!take((z0 + 1) & 1)) break;
+#pragma unroll
+        for (int q = 0; q < kRows3; ++q) cm[q] = sp[(z0 + 1) & 1][ty + 8 * q + 1][c + 1];
+        if (!take(z0 & 1)) break;
+#pragma unroll
+        for (int q = 0; q < kRows3; ++q) c0[q] = sp[z0 & 1][ty + 8 * q + 1][c + 1];
+        bool ok = true;
+        for (int z = z0; z < z1 && ok; ++z) {
+            const int b = z & 1, bn = b ^ 1;
+            ok = take(bn);                      // plane z + 1 (its buffer held z - 1, read)
+            if (!ok) break;
+            const float a3a = __ldg(cf3 + z), a3c = __ldg(cf3 + n3 + z), a3s = __ldg(cf3 + 2 * n3 + z);
+            uint32_t pos = (uint32_t)i1 + (uint32_t)a.p1 * (uint32_t)(a2 + ty) + pplane * (uint32_t)z;
+#pragma unroll
+            for (int q = 0; q < kRows3; ++q, pos += 8u * (uint32_t)a.p1) {
+                const int r = ty + 8 * q;
+                const float2 cp = sp[bn][r + 1][c + 1];
+                const float uh = c0[q].x, ul = c0[q].y;
+                const float u = uh + ul;
+                if (in1 && a2 + r < n2) {
+                    float acc;
+                    if (MANUF) {
+                        acc = mx::g32(a.g, u, a.t, (int64_t)i1 + (int64_t)n1 * (a2 + r) + (int64_t)plane * z);
+                    } else {
+                        acc = fmaf(fmaf(fmaf(a.g.f3, u, a.g.f2), u, a.g.f1), u, a.g.f0);
+                    }
+                    acc = fmaf(s12[q] + a3s, u, acc);
+                    acc = stencil_term(a1a, sp[b][r + 1][c], uh, ul, acc);
+                    acc = stencil_term(a1c, sp[b][r + 1][c + 2], uh, ul, acc);
+                    acc = stencil_term(a2a[q], sp[b][r][c + 1], uh, ul, acc);
+                    acc = stencil_term(a2c[q], sp[b][r + 2][c + 1], uh, ul, acc);
+                    acc = stencil_term(a3a, cm[q], uh, ul, acc);
+                    acc = stencil_term(a3c, cp, uh, ul, acc);
+                    uint32_t v[3];
+                    split_parts<F>(acc, 0.f, v);
+                    T* w = (T*)a.Wp + pos;
+                    w[0] = (T)v[0];
+                    w[pp] = (T)v[1];
+                    if (F::kAParts == 3) w[2 * pp] = (T)v[2];
+                }
+                cm[q] = c0[q];
+                c0[q] = cp;
+            }
+            __syncthreads();                    // before the next take overwrites plane z
+        }
+        if (!ok) break;
+    }
+    // never leave the block with copies in flight
+    if (threadIdx.x == 0)
+        for (int64_t k = consumed; k < issued; ++k)
+            tc::mbar_wait(tc::smem_u32(bars + (int)(k % kTmaStages)), (uint32_t)(k / kTmaStages) & 1, a.status);
+}
+
 __global__ void stencil_coef_kernel(const double* __restrict__ A, int n, float* coef) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double a = i > 0 ? A[i + (int64_t)n * (i - 1)] : 0.0;
@@ -462,6 +617,24 @@ int launch_prepass_mixed(const StencilArgsMixed& a0, float2* Up, cudaStream_t s)
         else if (!a.yadd && !a.yadd2 && !a.cadd && a.N < (int64_t(1) << 31) &&
                  (int64_t)a.part_pitch * (a.prec == MM_BF16X3 ? 3 : 2) < (int64_t(1) << 31)) {
             const bool manuf = a.g.kind == MM_G_ADR_MANUFACTURED;
+            // TMA-fed march when the state admits a 3-D FP64 tensor map (16-byte aligned
+            // base, even n1), else the register-prefetch march
+            CUtensorMap map;
+            const uint32_t box[3] = {(uint32_t)kRawX, (uint32_t)kRawY, 1};
+            if (encode_f64_box3(&map, a.U, a.n, box) == MM_OK) {
+                auto tk = a.prec == MM_BF16X3 ? (manuf ? stencil3d_tma_kernel<FormBF16, true>
+                                                       : stencil3d_tma_kernel<FormBF16, false>)
+                                              : (manuf ? stencil3d_tma_kernel<FormTF32, true>
+                                                       : stencil3d_tma_kernel<FormTF32, false>);
+                int per_sm = 0;
+                MM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tk, 256, kTmaSmem));
+                const int64_t steps = ((a.n[0] + kT1 - 1) / kT1) * ((a.n[1] + kT2 - 1) / kT2) * a.n[2];
+                const unsigned g3 =
+                    (unsigned)std::max<int64_t>(1, std::min<int64_t>(steps, (int64_t)num_sms() * std::max(per_sm, 1)));
+                tk<<<g3, 256, kTmaSmem, s>>>(map, a);
+                MM_LAUNCH_CHECK();
+                return MM_OK;
+            }
             auto kern = a.prec == MM_BF16X3 ? (manuf ? stencil3d_reg_kernel<FormBF16, true>
                                                      : stencil3d_reg_kernel<FormBF16, false>)
                                             : (manuf ? stencil3d_reg_kernel<FormTF32, true>
@@ -486,6 +659,21 @@ int launch_prepass_mixed(const StencilArgsMixed& a0, float2* Up, cudaStream_t s)
     TraceScope tr(KC_PREPASS, s);
     prepass_mixed_kernel<<<(unsigned)blocks, 256, 0, s>>>(a);
     MM_LAUNCH_CHECK();
+    return MM_OK;
+}
+
+int configure_prepass_kernels() {
+    static bool done = false;
+    if (done) return MM_OK;
+    MM_CUDA_TRY(cudaFuncSetAttribute(stencil3d_tma_kernel<FormBF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTmaSmem));
+    MM_CUDA_TRY(cudaFuncSetAttribute(stencil3d_tma_kernel<FormBF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTmaSmem));
+    MM_CUDA_TRY(cudaFuncSetAttribute(stencil3d_tma_kernel<FormTF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTmaSmem));
+    MM_CUDA_TRY(cudaFuncSetAttribute(stencil3d_tma_kernel<FormTF32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kTmaSmem));
+    done = true;
     return MM_OK;
 }
 

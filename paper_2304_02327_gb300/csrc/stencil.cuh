@@ -49,6 +49,7 @@ struct StencilArgsMixed {
     int prec;
     float t, ca, cb;
     PointwiseG g;
+    unsigned int* status;           // the plan's status word (a bounded wait that ran out)
 };
 
 // Runs split_pairs (U -> Up) and then the stencil; Up must hold N float2.
@@ -56,5 +57,8 @@ int launch_prepass_mixed(const StencilArgsMixed& a, float2* Up, cudaStream_t s);
 
 // [a | c | s] floats of a column-major tridiagonal n x n matrix (plan set-up).
 int build_stencil_coef(const double* A, int n, float* coef, cudaStream_t s);
+
+// Shared-memory attributes of the prepass kernels, set once outside any stream capture.
+int configure_prepass_kernels();
 
 }  // namespace mm

@@ -4,6 +4,7 @@
 // and returns false, so no kernel here can spin forever.
 #pragma once
 
+#include <cuda.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -61,6 +62,24 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
     if (status) atomicOr(status, MM_STATUS_TIMEOUT);
     return false;
+}
+
+// 3-D TMA tensor load of one box at coordinates (c0, c1, c2) of `map` into shared
+// memory at dst; completes its bytes on the mbarrier bar.  c0 x element size must be
+// a multiple of 16 bytes; boxes reaching outside the array read zeros.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before its later
+// async-proxy ones (a TMA load into a buffer the block has just read).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // ---- tensor memory -----------------------------------------------------

@@ -232,16 +232,6 @@ struct TcGroup {
     unsigned int* status;
 };
 
-// 3-D TMA load of one part tile: box {K block, box rows} at (k0, row0, part).
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int k0, int row0, int part,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(map), "r"(k0), "r"(row0), "r"(part), "r"(bar)
-        : "memory");
-}
-
 template <int E> struct PartType;
 template <> struct PartType<2> { using type = uint16_t; };
 template <> struct PartType<4> { using type = uint32_t; };
@@ -336,9 +326,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_const
                     tc::mbar_arrive_expect_tx(full(s), a_bytes + kBParts * b_tile);
                     const uint32_t st = tc::smem_u32(smem + s * stage_bytes);
                     for (int q = 0; q < F::kAParts; ++q)
-                        tma_load_3d(st + q * kATile, &k.xmap, kb * F::kBK, row0, q, full(s));
+                        tc::tma_load_3d(st + q * kATile, &k.xmap, kb * F::kBK, row0, q, full(s));
                     for (int part = 0; part < kBParts; ++part)   // rows col0.. of b0, b1, b2
-                        tma_load_3d(st + a_bytes + part * b_slot, &k.mmap, kb * F::kBK, col0, part, full(s));
+                        tc::tma_load_3d(st + a_bytes + part * b_slot, &k.mmap, kb * F::kBK, col0, part, full(s));
                     issued_last[s] = it;
                     if (++s == stages) { s = 0; ph ^= 1u; }
                 }
@@ -827,8 +817,25 @@ int tc_group_product(int prec, const TcClassSpec* cls, int ncls, const int* nc_c
     return launch_grouped<FormTF32>(cls, ncls, nc_cap, dev_tiles, ntiles, status, s);
 }
 
+int encode_f64_box3(CUtensorMap* map, const double* base, const int64_t* dims, const uint32_t* box) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return MM_ERR_UNSUPPORTED;
+    const uint64_t row = (uint64_t)dims[0] * 8, plane = row * (uint64_t)dims[1];
+    if (((uintptr_t)base & 15) || row % 16 || plane % 16 || (box[0] * 8) % 16) return MM_ERR_ARG;
+    const cuuint64_t d[3] = {(cuuint64_t)dims[0], (cuuint64_t)dims[1], (cuuint64_t)dims[2]};
+    const cuuint64_t st[2] = {(cuuint64_t)row, (cuuint64_t)plane};
+    const cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)base, d, st, bx, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+        return MM_ERR_CUDA;
+    return MM_OK;
+}
+
 int plan_prepare_tf32(mm_plan_s* p, cudaStream_t s) {
     if (!encode_fn()) return MM_ERR_UNSUPPORTED;
+    if (int rcp = configure_prepass_kernels()) return rcp;
     int rc0 = p->prec == MM_BF16X3 ? configure_kernel<FormBF16, 1>() : configure_kernel<FormTF32, 1>();
     if (!rc0) rc0 = p->prec == MM_BF16X3 ? configure_kernel<FormBF16, kMaxClasses>()
                                          : configure_kernel<FormTF32, kMaxClasses>();

@@ -2,6 +2,8 @@
 // steppers (expint_mixed.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include <vector>
 
 #include "plan.cuh"
@@ -17,6 +19,11 @@ struct PartView {
 };
 
 int form_elem_bytes(int prec);
+// A 3-D TMA map of a contiguous FP64 array with sizes dims[0] (fastest) x dims[1] x
+// dims[2], box box[0] x box[1] x box[2], no swizzle; loads past the array read zeros.
+// MM_ERR_ARG if the base is not 16-byte aligned or a row / plane pitch or the box's
+// rows are not a multiple of 16 bytes.
+int encode_f64_box3(CUtensorMap* map, const double* base, const int64_t* dims, const uint32_t* box);
 int form_parts(int prec);
 int form_pitch(int prec, int n);
 // Layout of the operand of mode mu (fibres along i_mu, rotated order).

@@ -259,3 +259,13 @@ def test_checkpoint_resume_is_bit_identical(api, form):
     api.expint_step(plan3, p.scheme, W, 3, t0=3 * p.tau, g=g3)
     torch.cuda.synchronize()
     assert torch.equal(U, W)
+
+
+@pytest.mark.parametrize("sizes", [(33, 20, 12), (40, 33, 24)])
+def test_mixed_3d_prepass_both_marches(api, form, sizes):
+    """The 3D K u + g prepass runs TMA-fed when the first direction is even (the FP64
+    rows are then 16-byte multiples) and register-fed otherwise: both against the
+    oracle, ETD2RK."""
+    p = wl.adr_3d(seed=8, steps=4, scheme=wl.ETD2RK, sizes=sizes)
+    got, ref = run_pair(api, p, form)
+    assert rel_err_inf(got, ref) <= TOL_STEP and rel_err_fro(got, ref) <= TOL_STEP
