@@ -269,3 +269,13 @@ def test_mixed_3d_prepass_both_marches(api, form, sizes):
     p = wl.adr_3d(seed=8, steps=4, scheme=wl.ETD2RK, sizes=sizes)
     got, ref = run_pair(api, p, form)
     assert rel_err_inf(got, ref) <= TOL_STEP and rel_err_fro(got, ref) <= TOL_STEP
+
+
+@pytest.mark.parametrize("sizes", [(2, 3, 5), (64, 1, 7), (1, 40, 3), (34, 33, 1)])
+def test_mixed_thin_3d_grids(api, form, sizes):
+    """Degenerate 3D grids (a direction of size 1 or 2, tiles far wider than the grid,
+    the zero-filled halo on every side) through both prepass marches and the
+    contraction, ETD2RK, against the oracle."""
+    p = wl.adr_3d(seed=9, steps=3, scheme=wl.ETD2RK, sizes=sizes)
+    got, ref = run_pair(api, p, form)
+    assert rel_err_inf(got, ref) <= TOL_STEP and rel_err_fro(got, ref) <= TOL_STEP
