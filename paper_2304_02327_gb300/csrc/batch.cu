@@ -6,10 +6,12 @@
 // input, the two phi_1 matrices of every instance in parts, the FP32 result -- so
 // that one pair of TMA maps per class addresses all of its instances.  A step is
 // four launches whatever the number of instances:
-//   prepass   W = K u + g(t, u) of every instance (chunks of one instance each)
+//   prepass   W = K u + g(t, u) of every instance (32 x 32 tiles)
 //   mode 1    one persistent tensor-core launch over the tiles of all classes
 //   mode 2    the same for the second direction, FP32 out
 //   update    u += tau y, FP64, every instance
+// and within a run the update of one step and the prepass of the next are one
+// launch (the state then alternates between the caller's buffers and a second set).
 // The tiles of a mode are ordered by decreasing cost and taken round-robin by one
 // CTA per SM.  The tile width (nc) is picked at creation by timing the candidate
 // tilings on the batch itself (mm_tune.autotune), and expint_batch_run captures
@@ -35,7 +37,8 @@ constexpr int kChunk = 8192;           // elements per chunk of the elementwise 
 constexpr int kNcCandidates[] = {160, 128, 96, 64};
 
 struct BInst {                         // device table, one entry per instance
-    double* U;
+    double* U;                         // the caller's state
+    double* S;                         // the other state buffer of the fused passes
     const float* coef1;                // [a | c | row sum] of the band of A_1, A_2
     const float* coef2;
     uint8_t* wbase;                    // class buffer of mode-1 inputs
@@ -48,97 +51,123 @@ struct BInst {                         // device table, one entry per instance
 
 // W = K u + g(t, u) in parts, the stencil from differences of the double-float
 // split of the state (the arithmetic of the single-problem mixed prepass, d = 2).
-// A 32 x 32 tile of one instance and its one-element halo are split once into
-// shared memory (each state value read and split ~1.1 times instead of five);
-// 256 threads, four rows each.  Tiles are numbered instance after instance
-// (tile_begin holds each instance's first tile) and each block takes one
-// contiguous range, so it locates its instance once and then walks forward.
+// Work unit: a 32 x 32 tile of one instance (a host table lists every tile, instance
+// after instance, {instance, a_1, a_2}); each block takes one contiguous range of
+// tiles.  A tile and its one-element halo are split once into the float2 plane sp,
+// so each state value is read and split ~1.13 times instead of five.  Thread
+// (lane c, warp w) owns column i_1 = a_1 + c and rows i_2 = a_2 + w + 8 q of the tile
+// (q = 0..3): it loads, splits and later evaluates exactly those four values, with
+// plain index arithmetic and coalesced rows; threads 0..131 also load one value each
+// of the halo ring (the rows above and below, the columns left and right).  The next
+// tile's values are loaded into registers while this one's stencil runs.
 constexpr int kT = 32;
-constexpr int kHalo = (kT + 2) * (kT + 2);          // 1156 values of a tile with its halo
-constexpr int kPer = (kHalo + 255) / 256;           // of them per thread
+constexpr int kW = kT + 2;                          // a tile with its halo, per side
+constexpr int kRing = 4 * kT + 4;                   // 132 halo values around a tile
+constexpr int kRowsPer = kT / 8;                    // rows of the tile per thread
 
-struct TileAt {
-    int inst, a1, a2;
-};
-
-__device__ __forceinline__ TileAt tile_at(const BInst* __restrict__ tab, const int64_t* __restrict__ tile_begin,
-                                          int inst, int64_t T) {
-    const int n1 = tab[inst].n1;
-    const int tiles1 = (n1 + kT - 1) / kT;
-    const int lt = (int)(T - __ldg(tile_begin + inst));
-    return TileAt{inst, (lt % tiles1) * kT, (lt / tiles1) * kT};
+// Halo ring position t = 0..131 -> (row, column) of the tile, both in [-1, 32]:
+// the row above (t < 34), the row below, the column left, the column right.
+__device__ __forceinline__ void ring_pos(int t, int& r, int& c) {
+    if (t < kW) { r = -1; c = t - 1; }
+    else if (t < 2 * kW) { r = kT; c = t - kW - 1; }
+    else if (t < 2 * kW + kT) { r = t - 2 * kW; c = -1; }
+    else { r = t - 2 * kW - kT; c = kT; }
 }
 
-template <class F>
+// FUSE: the previous step's update comes first: the state that the stencil sees is
+// u' = u + tau y (the update pass's FMA, from the state buffer `from` -- 0: U, 1: S --
+// and the previous Tucker result y), formed for every value of the tile and its halo,
+// and each tile writes its own values of u' to the other buffer (reads and writes
+// never touch the same buffer, so neighbouring tiles can run in any order).
+template <class F, bool FUSE>
 __global__ void __launch_bounds__(256, 4) batch_prepass_kernel(const BInst* __restrict__ tab,
-                                                            const int64_t* __restrict__ tile_begin, int count,
-                                                            int64_t ntiles) {
+                                                            const int4* __restrict__ tiles, int64_t ntiles,
+                                                            int from, unsigned int* status) {
     using PT = typename std::conditional<F::kElem == 4, uint32_t, uint16_t>::type;
-    __shared__ float2 sp[kT + 2][kT + 2];
+    __shared__ float2 sp[kW][kW];
     const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
     const int64_t T0 = blockIdx.x * per, T1 = min(ntiles, T0 + per);
     if (T0 >= T1) return;
-    int inst = 0, hi = count;                   // tile_begin[inst] <= T0 < tile_begin[hi]
-    while (hi - inst > 1) {
-        const int mid = (inst + hi) >> 1;
-        if (__ldg(tile_begin + mid) <= T0) inst = mid;
-        else hi = mid;
-    }
-    int64_t next = __ldg(tile_begin + inst + 1);
-    double raw[kPer];
-    // global loads of a tile's halo region, left in flight
-    auto fetch = [&](const TileAt& ta) {
-        const double* U = tab[ta.inst].U;
-        const int n1 = tab[ta.inst].n1, n2 = tab[ta.inst].n2;
+    const int c = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool ring = threadIdx.x < kRing;
+    int rr = 0, rc = 0;
+    if (ring) ring_pos(threadIdx.x, rr, rc);
+    double ui[kRowsPer], ur = 0.0;              // this thread's values of the tile, its ring value
+    float yi[FUSE ? kRowsPer : 1], yr = 0.f;
+    // global loads of a tile's values, left in flight (positions within an instance
+    // fit 32 bits)
+    auto fetch = [&](const int4 t) {
+        const BInst& bi = tab[t.x];
+        const double* U = (FUSE && from) ? bi.S : bi.U;
+        const float* y = bi.y;
+        const int n1 = bi.n1, n2 = bi.n2;
+        const int i1 = t.y + c;
+        const int o = i1 + n1 * (t.z + w);
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int e = threadIdx.x + 256 * k;
-            const int r = e / (kT + 2), c = e % (kT + 2);
-            const int i1 = ta.a1 - 1 + c, i2 = ta.a2 - 1 + r;
-            raw[k] = (e < kHalo && i1 >= 0 && i1 < n1 && i2 >= 0 && i2 < n2) ? __ldg(U + i1 + (int64_t)n1 * i2)
-                                                                             : 0.0;
+        for (int q = 0; q < kRowsPer; ++q) {
+            const bool in = i1 < n1 && t.z + w + 8 * q < n2;
+            ui[q] = in ? __ldg(U + (o + 8 * q * n1)) : 0.0;
+            if (FUSE) yi[FUSE ? q : 0] = in ? __ldg(y + (o + 8 * q * n1)) : 0.f;
+        }
+        if (ring) {
+            const int j1 = t.y + rc, j2 = t.z + rr;
+            const bool in = (unsigned)j1 < (unsigned)n1 && (unsigned)j2 < (unsigned)n2;
+            ur = in ? __ldg(U + (j1 + n1 * j2)) : 0.0;
+            if (FUSE) yr = in ? __ldg(y + (j1 + n1 * j2)) : 0.f;
         }
     };
-    TileAt cur = tile_at(tab, tile_begin, inst, T0);
+    int4 cur = __ldg(tiles + T0);
     fetch(cur);
-    const int c = threadIdx.x % kT;
+    bool bad = false;
     for (int64_t T = T0; T < T1; ++T) {
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int e = threadIdx.x + 256 * k;
-            if (e < kHalo) {
-                float2 v;
-                mx::d2ff(raw[k], v.x, v.y);
-                (&sp[0][0])[e] = v;
-            }
-        }
         // this tile's instance data (loaded before the stores below, which cannot
         // alias them once in registers)
-        const BInst& bi = tab[cur.inst];
+        const BInst& bi = tab[cur.x];
         const int n1 = bi.n1, n2 = bi.n2, p1 = bi.p1;
         const float* cf1 = bi.coef1;
         const float* cf2 = bi.coef2;
-        uint8_t* wbase = bi.wbase;
-        const int64_t wpp = bi.w_part_pitch, woff = bi.w_off;
+        PT* const wt = (PT*)bi.wbase + bi.w_off;
+        const int64_t wpp = bi.w_part_pitch;
         const float g0 = bi.g.f0, g1 = bi.g.f1, g2 = bi.g.f2, g3 = bi.g.f3;
-        const int a1 = cur.a1, a2 = cur.a2;
+        const int a1 = cur.y, a2 = cur.z;
+        const int i1 = a1 + c;
+        const bool in1 = i1 < n1;
+        float2 ctr[kRowsPer];                   // this thread's values, split
+#pragma unroll
+        for (int q = 0; q < kRowsPer; ++q) {
+            const int i2 = a2 + w + 8 * q;
+            double v = ui[q];
+            if (FUSE && in1 && i2 < n2) {
+                v = fma(bi.tau, mx::f2d(yi[FUSE ? q : 0]), v);
+                bad |= !mx::finite_bits(v);
+                (from ? bi.U : bi.S)[i1 + n1 * i2] = v;
+            }
+            mx::d2ff(v, ctr[q].x, ctr[q].y);
+            sp[w + 8 * q + 1][c + 1] = ctr[q];
+        }
+        if (ring) {
+            double v = ur;
+            const int j1 = a1 + rc, j2 = a2 + rr;
+            if (FUSE && (unsigned)j1 < (unsigned)n1 && (unsigned)j2 < (unsigned)n2)
+                v = fma(bi.tau, mx::f2d(yr), v);
+            float2 h;
+            mx::d2ff(v, h.x, h.y);
+            sp[rr + 1][rc + 1] = h;
+        }
         if (T + 1 < T1) {                // the next tile's loads overlap this tile's stencil
-            while (T + 1 >= next) next = __ldg(tile_begin + (++inst) + 1);
-            cur = tile_at(tab, tile_begin, inst, T + 1);
+            cur = __ldg(tiles + T + 1);
             fetch(cur);
         }
         // coefficients along i_1 are fixed for this thread's column of the tile
-        const int i1 = a1 + c;
-        const bool in1 = i1 < n1;
         const float c1a = in1 ? __ldg(cf1 + i1) : 0.f, c1c = in1 ? __ldg(cf1 + n1 + i1) : 0.f,
                     c1s = in1 ? __ldg(cf1 + 2 * n1 + i1) : 0.f;
         __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kT / 8; ++q) {
-            const int r = threadIdx.x / kT + 8 * q;
+        for (int q = 0; q < kRowsPer; ++q) {
+            const int r = w + 8 * q;
             const int i2 = a2 + r;
             if (!in1 || i2 >= n2) continue;
-            const float uh = sp[r + 1][c + 1].x, ul = sp[r + 1][c + 1].y;
+            const float uh = ctr[q].x, ul = ctr[q].y;
             const float u = uh + ul;
             // g is autonomous in a batch: 0 or a cubic (zero coefficients for g = 0)
             float acc = fmaf(fmaf(fmaf(g3, u, g2), u, g1), u, g0);
@@ -151,28 +180,31 @@ __global__ void __launch_bounds__(256, 4) batch_prepass_kernel(const BInst* __re
             acc = fmaf(__ldg(cf2 + n2 + i2), (sp[r + 2][c + 1].x - uh) + (sp[r + 2][c + 1].y - ul), acc);
             uint32_t v[3];
             split_parts<F>(acc, 0.f, v);
-            PT* w = (PT*)wbase + woff + i1 + (int64_t)p1 * i2;
-            w[0] = (PT)v[0];
-            w[wpp] = (PT)v[1];
-            if (F::kAParts == 3) w[2 * wpp] = (PT)v[2];
+            PT* wp = wt + (i1 + p1 * i2);
+            wp[0] = (PT)v[0];
+            wp[wpp] = (PT)v[1];
+            if (F::kAParts == 3) wp[2 * wpp] = (PT)v[2];
         }
         __syncthreads();
     }
+    if (FUSE && bad) atomicOr(status, MM_STATUS_NONFINITE);
 }
 
-// u += tau y (one DFMA per element), non-finite results flagged.
+// U = u + tau y (one DFMA per element) from the state buffer `from` (0: U itself,
+// 1: S), non-finite results flagged.
 __global__ void __launch_bounds__(256) batch_update_kernel(const BInst* __restrict__ tab,
                                                            const int4* __restrict__ chunks, int64_t nchunks,
-                                                           unsigned int* status) {
+                                                           int from, unsigned int* status) {
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int4 ch = chunks[c];
         double* U = tab[ch.x].U;        // loaded once: the stores to U cannot alias them
+        const double* src = from ? tab[ch.x].S : U;
         const float* y = tab[ch.x].y;
         const double tau = tab[ch.x].tau;
         bool bad = false;
         for (int e = threadIdx.x; e < ch.z; e += blockDim.x) {
             const int i = ch.y + e;
-            const double v = fma(tau, mx::f2d(__ldg(y + i)), U[i]);
+            const double v = fma(tau, mx::f2d(__ldg(y + i)), src[i]);
             bad |= !mx::finite_bits(v);
             U[i] = v;
         }
@@ -212,7 +244,7 @@ struct mm_batch_s {
     BInst* tab = nullptr;
     int4* chunks = nullptr;                 // update pass: {instance, start, length}
     int64_t nchunks = 0;
-    int64_t* tile_begin = nullptr;          // prepass: first 32 x 32 tile of each instance
+    int4* ptiles = nullptr;                 // prepass: {instance, a_1, a_2} of every 32 x 32 tile
     int64_t ntiles = 0;
     unsigned int* status = nullptr;
     int use_graph = 1;
@@ -265,27 +297,48 @@ int tucker_modes(mm_batch_s* b, cudaStream_t s) {
 
 int64_t ew_grid(const mm_batch_s* b) { return std::min<int64_t>(b->nchunks, (int64_t)num_sms() * 8); }
 
-int prepass(mm_batch_s* b, double t, cudaStream_t s) {
+typedef void (*PrepassKernel)(const BInst*, const int4*, int64_t, int, unsigned int*);
+PrepassKernel prepass_kernel_of(int prec, bool fuse) {
+    return prec == MM_BF16X3 ? (fuse ? batch_prepass_kernel<FormBF16, true> : batch_prepass_kernel<FormBF16, false>)
+                             : (fuse ? batch_prepass_kernel<FormTF32, true> : batch_prepass_kernel<FormTF32, false>);
+}
+
+// W = K u + g(u) of every instance (the batch's nonlinearities are autonomous);
+// fused: of u' = u + tau y from state buffer `from`, u' written to the other one.
+int prepass(mm_batch_s* b, bool fuse, int from, cudaStream_t s) {
     const int64_t grid = std::min<int64_t>(b->ntiles, (int64_t)num_sms() * 8);
     TraceScope tr(KC_PREPASS, s);
-    (void)t;   // the batch's nonlinearities are autonomous
-    if (b->prec == MM_BF16X3)
-        batch_prepass_kernel<FormBF16><<<(unsigned)grid, 256, 0, s>>>(b->tab, b->tile_begin, b->count, b->ntiles);
-    else
-        batch_prepass_kernel<FormTF32><<<(unsigned)grid, 256, 0, s>>>(b->tab, b->tile_begin, b->count, b->ntiles);
+    auto k = prepass_kernel_of(b->prec, fuse);
+    k<<<(unsigned)grid, 256, 0, s>>>(b->tab, b->ptiles, b->ntiles, from, b->status);
     MM_LAUNCH_CHECK();
     return MM_OK;
 }
 
-int one_step(mm_batch_s* b, double t, cudaStream_t s) {
-    int rc0 = prepass(b, t, s);
-    if (rc0) return rc0;
-    int rc = tucker_modes(b, s);
-    if (rc) return rc;
+int update(mm_batch_s* b, int from, cudaStream_t s) {
     TraceScope tr(KC_SPLIT, s);
-    batch_update_kernel<<<(unsigned)ew_grid(b), 256, 0, s>>>(b->tab, b->chunks, b->nchunks, b->status);
+    batch_update_kernel<<<(unsigned)ew_grid(b), 256, 0, s>>>(b->tab, b->chunks, b->nchunks, from, b->status);
     MM_LAUNCH_CHECK();
     return MM_OK;
+}
+
+// nsteps exponential Euler steps from the caller's states U back into U.  Between two
+// steps the update u + tau y is fused into the next step's prepass, which reads one
+// state buffer and writes the other (U, S, U, ...); the last step's update writes U
+// (in place, or from S).  The arithmetic of every value is that of separate passes.
+int run_steps(mm_batch_s* b, int nsteps, cudaStream_t s) {
+    int from = 0;                        // the buffer that holds the current state
+    int rc = prepass(b, false, 0, s);
+    for (int k = 0; k < nsteps && !rc; ++k) {
+        rc = tucker_modes(b, s);
+        if (rc) break;
+        if (k + 1 < nsteps) {
+            rc = prepass(b, true, from, s);
+            from ^= 1;
+        } else {
+            rc = update(b, from, s);
+        }
+    }
+    return rc;
 }
 
 // Mean time of `reps` runs of fn after one warm-up run, in ms.
@@ -478,6 +531,10 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
         const int cnt = (int)C.members.size();
         const int p1 = form_pitch(prec, C.n1), p2 = form_pitch(prec, C.n2);
         const int64_t nn = (int64_t)C.n1 * C.n2;
+        if ((int64_t)p1 * C.n2 >= (int64_t(1) << 31)) {    // 32-bit positions within an instance
+            rc = MM_ERR_SHAPE;
+            goto fail;
+        }
         if (!b->alloc((void**)&C.W, matrix_parts_bytes(prec, (int64_t)cnt * C.n2, C.n1, AP)) ||
             !b->alloc((void**)&C.P, matrix_parts_bytes(prec, (int64_t)cnt * C.n1, C.n2, AP)) ||
             !b->alloc((void**)&C.phi1, matrix_parts_bytes(prec, (int64_t)cnt * C.n1, C.n1, 3)) ||
@@ -565,12 +622,25 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
     }
     b->nchunks = (int64_t)chunks.size();
     {
-        std::vector<int64_t> tb(count + 1, 0);
+        // the second state buffer of the fused passes, instance after instance
+        double* S = nullptr;
+        if (!b->alloc((void**)&S, (size_t)b->total_dof * sizeof(double))) {
+            rc = MM_ERR_NOMEM;
+            goto fail;
+        }
+        for (int j = 0; j < count; ++j) {
+            tab[j].S = S;
+            S += n1[j] * n2[j];
+        }
+    }
+    {
+        std::vector<int4> pt;
         for (int j = 0; j < count; ++j)
-            tb[j + 1] = tb[j] + ((n1[j] + kT - 1) / kT) * ((n2[j] + kT - 1) / kT);
-        b->ntiles = tb[count];
-        if (!b->alloc((void**)&b->tile_begin, tb.size() * sizeof(int64_t)) ||
-            cudaMemcpyAsync(b->tile_begin, tb.data(), tb.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s) !=
+            for (int a2 = 0; a2 < n2[j]; a2 += kT)
+                for (int a1 = 0; a1 < n1[j]; a1 += kT) pt.push_back(make_int4(j, a1, a2, 0));
+        b->ntiles = (int64_t)pt.size();
+        if (!b->alloc((void**)&b->ptiles, pt.size() * sizeof(int4)) ||
+            cudaMemcpyAsync(b->ptiles, pt.data(), pt.size() * sizeof(int4), cudaMemcpyHostToDevice, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             rc = MM_ERR_NOMEM;
@@ -601,7 +671,7 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
     }
     if (tune && tune->autotune && !tune->nc_cap) {
         // W from the initial states so the timed products see real operands
-        rc = prepass(b, 0.0, s);
+        rc = prepass(b, false, 0, s);
         if (rc) goto fail;
         rc = autotune(b, s);
         if (rc) goto fail;
@@ -622,13 +692,7 @@ extern "C" int expint_batch_run(mm_batch b, double t0, int nsteps, void* stream)
     if (!b || nsteps < 0 || !isfinite(t0)) return MM_ERR_ARG;
     if (nsteps == 0) return MM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!b->use_graph) {
-        for (int k = 0; k < nsteps; ++k) {
-            int rc = one_step(b, t0, s);
-            if (rc) return rc;
-        }
-        return MM_OK;
-    }
+    if (!b->use_graph) return run_steps(b, nsteps, s);
     if (!b->exec || b->exec_steps != nsteps) {
         if (b->exec) {
             cudaGraphExecDestroy(b->exec);
@@ -637,7 +701,7 @@ extern "C" int expint_batch_run(mm_batch b, double t0, int nsteps, void* stream)
         cudaGraph_t graph = nullptr;
         MM_CUDA_TRY(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
         int rc = MM_OK;
-        for (int k = 0; k < nsteps && !rc; ++k) rc = one_step(b, t0, b->cap);
+        rc = run_steps(b, nsteps, b->cap);
         const cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
         if (rc || ce != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -655,7 +719,7 @@ extern "C" int expint_batch_run(mm_batch b, double t0, int nsteps, void* stream)
     // the launches inside the graph, for the launch counters
     trace_count(KC_PREPASS, nsteps);
     trace_count(KC_CONTRACT_TF32, (long long)nsteps * 2 * (long long)b->launches.size());
-    trace_count(KC_SPLIT, nsteps);
+    trace_count(KC_SPLIT, 1);
     return MM_OK;
 }
 

@@ -15,15 +15,17 @@
 namespace mm {
 namespace mx {
 
-// Exact widening FP32 -> FP64 by bit manipulation (FP32 subnormals flush to 0).
+// Exact widening FP32 -> FP64 by bit manipulation (FP32 subnormals flush to 0), on
+// the two 32-bit words with selects (no branch): the exponent rebased by 896 (0x7ff
+// for inf / nan), the 23 mantissa bits shifted up by 29 across the two words.
 __device__ __forceinline__ double f2d(float f) {
     const uint32_t b = __float_as_uint(f);
-    const uint64_t s = (uint64_t)(b >> 31) << 63;
     const uint32_t e = (b >> 23) & 0xffu;
-    const uint64_t m = (uint64_t)(b & 0x7fffffu) << 29;
-    if (e == 0) return __longlong_as_double((long long)s);
-    if (e == 0xffu) return __longlong_as_double((long long)(s | 0x7ff0000000000000ull | m));
-    return __longlong_as_double((long long)(s | ((uint64_t)(e + 896u) << 52) | m));
+    const uint32_t m = b & 0x7fffffu;
+    const uint32_t eh = e == 0xffu ? 0x7ffu : e + 896u;
+    const uint32_t hi = (b & 0x80000000u) | (e == 0 ? 0u : (eh << 20) | (m >> 3));
+    const uint32_t lo = e == 0 ? 0u : m << 29;
+    return __hiloint2double((int)hi, (int)lo);
 }
 
 // x ~ hi + lo with hi = x truncated to 24 significant bits and lo = the next 23

@@ -92,6 +92,26 @@ def test_batch_graph_and_plain_launches_agree(api, form):
         assert torch.equal(a, c)
 
 
+@pytest.mark.parametrize("graph", [True, False])
+def test_batch_runs_split_anywhere_agree_bitwise(api, form, graph):
+    """Inside a run, each step's update is fused into the next step's prepass and the
+    state alternates between the caller's buffers and a second set; the last update
+    writes the caller's buffers in place (an even number of fused passes) or from the
+    second set (odd).  A run of 5 steps, runs of 2 + 3, of 4 + 1 and five runs of one
+    step must all give the same states bit for bit."""
+    probs = small_batch(steps=5)
+    ref, _ = run_batch(api, probs, form, 5, autotune=False, nc_cap=128, graph=graph)
+    for split in ((2, 3), (4, 1), (1, 1, 1, 1, 1)):
+        plans, gs, Us = api.setup_batch(probs, form)
+        b = api.Batch(plans, gs, Us, autotune=False, nc_cap=128, graph=graph)
+        for k in split:
+            b.run(k)
+        torch.cuda.synchronize()
+        assert b.status() == 0
+        for a, u, p in zip(ref, Us, probs):
+            np.testing.assert_array_equal(a, u.cpu().numpy(), err_msg=f"{p.name} {split}")
+
+
 def test_batch_autotune_picks_a_candidate(api, form):
     """The autotuner's schedule: a candidate width per size class, kept per class only
     when faster than the best uniform width; the tuned batch still reproduces the
