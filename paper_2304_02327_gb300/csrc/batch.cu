@@ -36,17 +36,19 @@ namespace {
 constexpr int kChunk = 8192;           // elements per chunk of the elementwise passes
 constexpr int kNcCandidates[] = {160, 128, 96, 64};
 
-struct BInst {                         // device table, one entry per instance
+// Device table, one 96-byte entry per instance, fields used together side by side
+// (the kernels read an entry with a few 16-byte loads).
+struct alignas(16) BInst {
     double* U;                         // the caller's state
     double* S;                         // the other state buffer of the fused passes
+    float* y;                          // this instance's FP32 Tucker result
+    uint8_t* w0;                       // its mode-1 input, part 0 (part q at q w_part_pitch elements)
     const float* coef1;                // [a | c | row sum] of the band of A_1, A_2
     const float* coef2;
-    uint8_t* wbase;                    // class buffer of mode-1 inputs
-    float* y;                          // this instance's FP32 Tucker result
-    int64_t w_part_pitch, w_off;
-    int n1, n2, p1;
+    int64_t w_part_pitch;
     double tau;
-    PointwiseG g;
+    int n1, n2, p1, pad;
+    float g0, g1, g2, g3;              // g = g0 + g1 u + g2 u^2 + g3 u^3 in FP32 (zeros: g = 0)
 };
 
 // W = K u + g(t, u) in parts, the stencil from differences of the double-float
@@ -126,9 +128,9 @@ __global__ void __launch_bounds__(256, 4) batch_prepass_kernel(const BInst* __re
         const int n1 = bi.n1, n2 = bi.n2, p1 = bi.p1;
         const float* cf1 = bi.coef1;
         const float* cf2 = bi.coef2;
-        PT* const wt = (PT*)bi.wbase + bi.w_off;
+        PT* const wt = (PT*)bi.w0;
         const int64_t wpp = bi.w_part_pitch;
-        const float g0 = bi.g.f0, g1 = bi.g.f1, g2 = bi.g.f2, g3 = bi.g.f3;
+        const float g0 = bi.g0, g1 = bi.g1, g2 = bi.g2, g3 = bi.g3;
         const int a1 = cur.y, a2 = cur.z;
         const int i1 = a1 + c;
         const bool in1 = i1 < n1;
@@ -588,13 +590,13 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
             e.U = U[j];
             e.coef1 = p->coef3f[0];
             e.coef2 = p->coef3f[1];
-            e.wbase = C.W;
+            e.w0 = C.W + (size_t)k * C.n2 * p1 * E;
             e.w_part_pitch = m1.X.part_pitch;
-            e.w_off = (int64_t)k * C.n2 * p1;
             e.y = C.y + (int64_t)k * nn;
-            e.n1 = C.n1; e.n2 = C.n2; e.p1 = p1;
+            e.n1 = C.n1; e.n2 = C.n2; e.p1 = p1; e.pad = 0;
             e.tau = p->tau;
-            e.g = pointwise_of(g ? &g[j] : nullptr);
+            const PointwiseG pg = pointwise_of(g ? &g[j] : nullptr);
+            e.g0 = pg.f0; e.g1 = pg.f1; e.g2 = pg.f2; e.g3 = pg.f3;
             for (int64_t s0 = 0; s0 < nn; s0 += kChunk)
                 chunks.push_back(make_int4(j, (int)s0, (int)std::min<int64_t>(kChunk, nn - s0), 0));
             b->total_dof += nn;
