@@ -449,7 +449,9 @@ template <class F, bool MANUF>
 __global__ void __launch_bounds__(256, 3) stencil3d_tma_kernel(const __grid_constant__ CUtensorMap map,
                                                                StencilArgsMixed a) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    // 128-byte aligned, by an offset on the shared array itself so that the compiler
+    // keeps shared-memory instructions for the accesses below
+    uint8_t* sm = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
     float2(*sp)[kT2 + 2][kT1 + 2] = (float2(*)[kT2 + 2][kT1 + 2])(sm + kTmaStages * kRawStride);
     uint64_t* bars = (uint64_t*)(sm + kTmaStages * kRawStride + kSplitBytes);
     __shared__ int fail;

@@ -257,7 +257,7 @@ __device__ __forceinline__ TileId tile_of(const TcGroup<C>& g, int64_t t) {
 template <class F, int C>
 __global__ void __launch_bounds__(kThreads, 1) tc_mode_kernel(const __grid_constant__ TcGroup<C> g) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);   // 1024-byte aligned
     const uint32_t b_slot = (uint32_t)g.stage_nc * kRowBytes;  // one part of the matrix tile
     const uint32_t a_bytes = F::kAParts * kATile;
     const uint32_t stage_bytes = a_bytes + kBParts * b_slot;
