@@ -432,18 +432,44 @@ __global__ void __launch_bounds__(256, 3) stencil3d_reg_kernel(StencilArgsMixed 
 // planes (each the 36 x 34 box at (a1 - 2, a2 - 1, z), so that the box starts on a
 // 16-byte boundary; rows and planes outside the array read zeros, which is the
 // Dirichlet halo), filled up to kTmaStages planes ahead by thread 0, so that many
-// loads are in flight per block without holding them in registers; each plane is
-// split once from the ring into the two float2 planes of stencil3d_reg_kernel.  The
-// arithmetic, its order and the work balance are stencil3d_reg_kernel's.  Every wait
-// on a plane is bounded: on timeout the status word gets MM_STATUS_TIMEOUT, the block
-// stops after its next barrier, and thread 0 waits (bounded) for its copies in flight.
+// loads are in flight per block without holding them in registers.  The arithmetic of
+// every output and its order are stencil3d_reg_kernel's, and so is the work balance;
+// the work is laid out for fewer instructions per element: each thread owns two
+// adjacent columns (i_1 = a1 + 2 cp, + 1; n1 is even on this path) of two rows, so it
+// reads its neighbours with 16-byte shared loads and writes two parts per 32-bit
+// (BF16) or 64-bit (TF32) store; the split planes keep the raw box's column index
+// (column i_1 at i_1 - a1 + 2) and are split two values at a time.  Every wait on a
+// plane is bounded: on timeout the status word gets MM_STATUS_TIMEOUT, the block stops
+// after its next barrier, and thread 0 waits (bounded) for its copies in flight.
 constexpr int kTmaStages = 4;
 constexpr int kRawX = kT1 + 4;                                   // 36 doubles: a1 - 2 .. a1 + 33
 constexpr int kRawY = kT2 + 2;                                   // 34 rows: a2 - 1 .. a2 + 32
 constexpr uint32_t kRawBytes = kRawX * kRawY * 8;                // 9792 bytes per plane
 constexpr uint32_t kRawStride = (kRawBytes + 127) / 128 * 128;
-constexpr uint32_t kSplitBytes = 2 * (kT2 + 2) * (kT1 + 2) * sizeof(float2);
-constexpr size_t kTmaSmem = 128 + kTmaStages * kRawStride + kSplitBytes + kTmaStages * 8;
+constexpr int kPairs = kRawY * (kRawX / 2);                      // 612 value pairs per plane
+constexpr int kPairsPer = (kPairs + 255) / 256;
+constexpr uint32_t kPlaneBytes = kRawY * kRawX * sizeof(float2);  // one split plane, 36 columns
+constexpr size_t kTmaSmem = 128 + kTmaStages * kRawStride + 2 * kPlaneBytes + kTmaStages * 8;
+
+template <class F>
+__device__ __forceinline__ void store_pair(uint8_t* W, uint32_t pos, uint32_t pp, float x0, float x1) {
+    uint32_t v0[3], v1[3];
+    split_parts<F>(x0, 0.f, v0);
+    split_parts<F>(x1, 0.f, v1);
+    if (F::kElem == 2) {
+        uint32_t* w = (uint32_t*)((uint16_t*)W + pos);
+        const uint32_t step = pp >> 1;                           // parts pp elements apart
+        w[0] = v0[0] | (v1[0] << 16);
+        w[step] = v0[1] | (v1[1] << 16);
+        if (F::kAParts == 3) w[2 * step] = v0[2] | (v1[2] << 16);
+    } else {
+        uint2* w = (uint2*)((uint32_t*)W + pos);
+        const uint32_t step = pp >> 1;
+        w[0] = make_uint2(v0[0], v1[0]);
+        w[step] = make_uint2(v0[1], v1[1]);
+        if (F::kAParts == 3) w[2 * step] = make_uint2(v0[2], v1[2]);
+    }
+}
 
 template <class F, bool MANUF>
 __global__ void __launch_bounds__(256, 3) stencil3d_tma_kernel(const __grid_constant__ CUtensorMap map,
@@ -452,19 +478,24 @@ __global__ void __launch_bounds__(256, 3) stencil3d_tma_kernel(const __grid_cons
     // 128-byte aligned, by an offset on the shared array itself so that the compiler
     // keeps shared-memory instructions for the accesses below
     uint8_t* sm = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
-    float2(*sp)[kT2 + 2][kT1 + 2] = (float2(*)[kT2 + 2][kT1 + 2])(sm + kTmaStages * kRawStride);
-    uint64_t* bars = (uint64_t*)(sm + kTmaStages * kRawStride + kSplitBytes);
+    float2(*sp)[kRawY][kRawX] = (float2(*)[kRawY][kRawX])(sm + kTmaStages * kRawStride);
+    uint64_t* bars = (uint64_t*)(sm + kTmaStages * kRawStride + 2 * kPlaneBytes);
     __shared__ int fail;
-    using T = typename std::conditional<F::kElem == 4, uint32_t, uint16_t>::type;
     const int n1 = (int)a.n[0], n2 = (int)a.n[1], n3 = (int)a.n[2];
     const int t1 = (n1 + kT1 - 1) / kT1, t2 = (n2 + kT2 - 1) / kT2;
     const uint32_t plane = (uint32_t)n1 * (uint32_t)n2;
-    const uint32_t pplane = (uint32_t)a.p1 * (uint32_t)n2;
+    const uint32_t p1 = (uint32_t)a.p1;
+    const uint32_t pplane = p1 * (uint32_t)n2;
     const uint32_t pp = (uint32_t)a.part_pitch;
+    uint8_t* const Wp = a.Wp;
+    const float gf0 = a.g.f0, gf1 = a.g.f1, gf2 = a.g.f2, gf3 = a.g.f3;
     const float* cf1 = a.coef[0];
     const float* cf2 = a.coef[1];
     const float* cf3 = a.coef[2];
-    const int c = threadIdx.x % kT1, ty = threadIdx.x / kT1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cp = lane & 15;                 // column pair: tile columns 2 cp, 2 cp + 1
+    const int r0 = (lane >> 4) + 2 * w;       // rows r0 and r0 + 16 of the tile
+    const int j0 = 2 * cp + 2;                // their index in the split planes
     if (threadIdx.x == 0) {
         for (int st = 0; st < kTmaStages; ++st) tc::mbar_init(tc::smem_u32(bars + st), 1);
         tc::fence_mbar_init();
@@ -492,20 +523,22 @@ __global__ void __launch_bounds__(256, 3) stencil3d_tma_kernel(const __grid_cons
             tc::fence_proxy_async_smem();
             for (; issued < first + min((int64_t)kTmaStages, nplanes); ++issued) issue(issued);
         }
-        // take the next plane from the ring and split it into float2 plane buf
+        // take the next plane from the ring and split it, two values at a time, into
+        // float2 plane buf (the raw box's column index kept)
         auto take = [&](int buf) -> bool {
             const int st = (int)(consumed % kTmaStages);
             if (!tc::mbar_wait(tc::smem_u32(bars + st), (uint32_t)(consumed / kTmaStages) & 1, a.status)) fail = 1;
-            const double* rp = (const double*)(sm + st * kRawStride);
-            float2* dst = &sp[buf][0][0];
+            const double2* rp = (const double2*)(sm + st * kRawStride);
+            float4* dst = (float4*)&sp[buf][0][0];
 #pragma unroll
-            for (int k = 0; k < kPer3; ++k) {
+            for (int k = 0; k < kPairsPer; ++k) {
                 const int e = threadIdx.x + 256 * k;
-                if (e < kHalo3) {
-                    const int r = e / (kT1 + 2), cc = e % (kT1 + 2);
-                    float2 v;
-                    mx::d2ff(rp[r * kRawX + cc + 1], v.x, v.y);
-                    dst[e] = v;
+                if (e < kPairs) {
+                    const double2 v = rp[e];
+                    float4 h;
+                    mx::d2ff(v.x, h.x, h.y);
+                    mx::d2ff(v.y, h.z, h.w);
+                    dst[e] = h;
                 }
             }
             ++consumed;
@@ -516,62 +549,80 @@ __global__ void __launch_bounds__(256, 3) stencil3d_tma_kernel(const __grid_cons
             }
             return fail == 0;
         };
-        const int i1 = a1 + c;
-        const bool in1 = i1 < n1;
-        const float a1a = in1 ? __ldg(cf1 + i1) : 0.f, a1c = in1 ? __ldg(cf1 + n1 + i1) : 0.f;
-        const float a1s = in1 ? __ldg(cf1 + 2 * n1 + i1) : 0.f;
-        float a2a[kRows3], a2c[kRows3], s12[kRows3];
+        // coefficients along i_1 and i_2 are fixed for this thread's outputs
+        const int i1 = a1 + 2 * cp;
+        const bool in1 = i1 < n1;               // n1 even: both columns, or neither
+        float c1a[2], c1c[2], c1s[2];
 #pragma unroll
-        for (int q = 0; q < kRows3; ++q) {
-            const int i2 = a2 + ty + 8 * q;
-            const bool in2 = i2 < n2;
-            a2a[q] = in2 ? __ldg(cf2 + i2) : 0.f;
-            a2c[q] = in2 ? __ldg(cf2 + n2 + i2) : 0.f;
-            s12[q] = a1s + (in2 ? __ldg(cf2 + 2 * n2 + i2) : 0.f);
+        for (int j = 0; j < 2; ++j) {
+            c1a[j] = in1 ? __ldg(cf1 + i1 + j) : 0.f;
+            c1c[j] = in1 ? __ldg(cf1 + n1 + i1 + j) : 0.f;
+            c1s[j] = in1 ? __ldg(cf1 + 2 * n1 + i1 + j) : 0.f;
         }
-        float2 cm[kRows3], c0[kRows3];
+        float c2a[2], c2c[2], s12[2][2];
+        bool in2[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i2 = a2 + r0 + 16 * q;
+            in2[q] = i2 < n2;
+            c2a[q] = in2[q] ? __ldg(cf2 + i2) : 0.f;
+            c2c[q] = in2[q] ? __ldg(cf2 + n2 + i2) : 0.f;
+            const float c2s = in2[q] ? __ldg(cf2 + 2 * n2 + i2) : 0.f;
+            s12[q][0] = c1s[0] + c2s;
+            s12[q][1] = c1s[1] + c2s;
+        }
+        // centres of planes z - 1 (cm) and z (c0) of this thread's outputs, [q][column]
+        float4 cm[2], c0[2];
         if (!take((z0 + 1) & 1)) break;
 #pragma unroll
-        for (int q = 0; q < kRows3; ++q) cm[q] = sp[(z0 + 1) & 1][ty + 8 * q + 1][c + 1];
+        for (int q = 0; q < 2; ++q) cm[q] = *(const float4*)&sp[(z0 + 1) & 1][r0 + 16 * q + 1][j0];
         if (!take(z0 & 1)) break;
 #pragma unroll
-        for (int q = 0; q < kRows3; ++q) c0[q] = sp[z0 & 1][ty + 8 * q + 1][c + 1];
+        for (int q = 0; q < 2; ++q) c0[q] = *(const float4*)&sp[z0 & 1][r0 + 16 * q + 1][j0];
         bool ok = true;
         for (int z = z0; z < z1 && ok; ++z) {
             const int b = z & 1, bn = b ^ 1;
             ok = take(bn);                      // plane z + 1 (its buffer held z - 1, read)
             if (!ok) break;
             const float a3a = __ldg(cf3 + z), a3c = __ldg(cf3 + n3 + z), a3s = __ldg(cf3 + 2 * n3 + z);
-            uint32_t pos = (uint32_t)i1 + (uint32_t)a.p1 * (uint32_t)(a2 + ty) + pplane * (uint32_t)z;
 #pragma unroll
-            for (int q = 0; q < kRows3; ++q, pos += 8u * (uint32_t)a.p1) {
-                const int r = ty + 8 * q;
-                const float2 cp = sp[bn][r + 1][c + 1];
-                const float uh = c0[q].x, ul = c0[q].y;
-                const float u = uh + ul;
-                if (in1 && a2 + r < n2) {
-                    float acc;
-                    if (MANUF) {
-                        acc = mx::g32(a.g, u, a.t, (int64_t)i1 + (int64_t)n1 * (a2 + r) + (int64_t)plane * z);
-                    } else {
-                        acc = fmaf(fmaf(fmaf(a.g.f3, u, a.g.f2), u, a.g.f1), u, a.g.f0);
+            for (int q = 0; q < 2; ++q) {
+                const int r = r0 + 16 * q;
+                const float4 cpn = *(const float4*)&sp[bn][r + 1][j0];           // plane z + 1
+                if (in1 && in2[q]) {
+                    const float2 lft = sp[b][r + 1][j0 - 1], rgt = sp[b][r + 1][j0 + 2];
+                    const float4 up = *(const float4*)&sp[b][r][j0];
+                    const float4 dn = *(const float4*)&sp[b][r + 2][j0];
+                    const float2 ctr[2] = {make_float2(c0[q].x, c0[q].y), make_float2(c0[q].z, c0[q].w)};
+                    const float2 nbl[2] = {lft, ctr[0]}, nbr[2] = {ctr[1], rgt};
+                    const float2 nbu[2] = {make_float2(up.x, up.y), make_float2(up.z, up.w)};
+                    const float2 nbd[2] = {make_float2(dn.x, dn.y), make_float2(dn.z, dn.w)};
+                    const float2 nbm[2] = {make_float2(cm[q].x, cm[q].y), make_float2(cm[q].z, cm[q].w)};
+                    const float2 nbp[2] = {make_float2(cpn.x, cpn.y), make_float2(cpn.z, cpn.w)};
+                    float out[2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const float uh = ctr[j].x, ul = ctr[j].y;
+                        const float u = uh + ul;
+                        float acc;
+                        if (MANUF) {
+                            acc = mx::g32(a.g, u, a.t, (int64_t)(i1 + j) + (int64_t)n1 * (a2 + r) + (int64_t)plane * z);
+                        } else {
+                            acc = fmaf(fmaf(fmaf(gf3, u, gf2), u, gf1), u, gf0);
+                        }
+                        acc = fmaf(s12[q][j] + a3s, u, acc);
+                        acc = stencil_term(c1a[j], nbl[j], uh, ul, acc);
+                        acc = stencil_term(c1c[j], nbr[j], uh, ul, acc);
+                        acc = stencil_term(c2a[q], nbu[j], uh, ul, acc);
+                        acc = stencil_term(c2c[q], nbd[j], uh, ul, acc);
+                        acc = stencil_term(a3a, nbm[j], uh, ul, acc);
+                        acc = stencil_term(a3c, nbp[j], uh, ul, acc);
+                        out[j] = acc;
                     }
-                    acc = fmaf(s12[q] + a3s, u, acc);
-                    acc = stencil_term(a1a, sp[b][r + 1][c], uh, ul, acc);
-                    acc = stencil_term(a1c, sp[b][r + 1][c + 2], uh, ul, acc);
-                    acc = stencil_term(a2a[q], sp[b][r][c + 1], uh, ul, acc);
-                    acc = stencil_term(a2c[q], sp[b][r + 2][c + 1], uh, ul, acc);
-                    acc = stencil_term(a3a, cm[q], uh, ul, acc);
-                    acc = stencil_term(a3c, cp, uh, ul, acc);
-                    uint32_t v[3];
-                    split_parts<F>(acc, 0.f, v);
-                    T* w = (T*)a.Wp + pos;
-                    w[0] = (T)v[0];
-                    w[pp] = (T)v[1];
-                    if (F::kAParts == 3) w[2 * pp] = (T)v[2];
+                    store_pair<F>(Wp, (uint32_t)i1 + p1 * (uint32_t)(a2 + r) + pplane * (uint32_t)z, pp, out[0], out[1]);
                 }
                 cm[q] = c0[q];
-                c0[q] = cp;
+                c0[q] = cpn;
             }
             __syncthreads();                    // before the next take overwrites plane z
         }
