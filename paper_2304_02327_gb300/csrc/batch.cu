@@ -192,6 +192,168 @@ __global__ void __launch_bounds__(256, 4) batch_prepass_kernel(const BInst* __re
     if (FUSE && bad) atomicOr(status, MM_STATUS_NONFINITE);
 }
 
+// The same pass with two adjacent columns per thread, for batches whose every
+// instance has an even n_1 and 16-byte aligned states (then every pair of a row starts
+// on a 16-byte boundary): thread (lane, warp) owns columns 2 cp, 2 cp + 1 (cp = lane
+// mod 16) of rows r0 = lane / 16 + 2 warp and r0 + 16, loads and stores state pairs with
+// 16-byte accesses, reads its neighbours with 16-byte shared loads from a split plane
+// whose column c sits at index c + 2, and stores the parts of two outputs per 32-bit
+// (BF16) or 64-bit (TF32) store.  Every output's arithmetic and its order are
+// batch_prepass_kernel's, so the two kernels agree bit for bit.
+template <class F, bool FUSE>
+__global__ void __launch_bounds__(256, 4) batch_prepass2_kernel(const BInst* __restrict__ tab,
+                                                             const int4* __restrict__ tiles, int64_t ntiles,
+                                                             int from, unsigned int* status) {
+    constexpr int kPW = kT + 4;                     // split-plane row: halo, 32 columns, halo, pad
+    __shared__ __align__(16) float2 sp[kW][kPW];
+    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int64_t T0 = blockIdx.x * per, T1 = min(ntiles, T0 + per);
+    if (T0 >= T1) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int cp = lane & 15, r0 = (lane >> 4) + 2 * w, j0 = 2 * cp + 2;
+    const bool ring = threadIdx.x < kRing;
+    int rr = 0, rc = 0;
+    if (ring) ring_pos(threadIdx.x, rr, rc);
+    double2 ui[2];
+    double ur = 0.0;
+    float2 yi[FUSE ? 2 : 1];
+    float yr = 0.f;
+    auto fetch = [&](const int4 t) {
+        const BInst& bi = tab[t.x];
+        const double* U = (FUSE && from) ? bi.S : bi.U;
+        const float* y = bi.y;
+        const int n1 = bi.n1, n2 = bi.n2;
+        const int i1 = t.y + 2 * cp;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int i2 = t.z + r0 + 16 * q;
+            const bool in = i1 < n1 && i2 < n2;
+            const int o = i1 + n1 * i2;
+            ui[q] = in ? __ldg((const double2*)(U + o)) : make_double2(0.0, 0.0);
+            if (FUSE) yi[FUSE ? q : 0] = in ? __ldg((const float2*)(y + o)) : make_float2(0.f, 0.f);
+        }
+        if (ring) {
+            const int j1 = t.y + rc, j2 = t.z + rr;
+            const bool in = (unsigned)j1 < (unsigned)n1 && (unsigned)j2 < (unsigned)n2;
+            ur = in ? __ldg(U + (j1 + n1 * j2)) : 0.0;
+            if (FUSE) yr = in ? __ldg(y + (j1 + n1 * j2)) : 0.f;
+        }
+    };
+    int4 cur = __ldg(tiles + T0);
+    fetch(cur);
+    bool bad = false;
+    for (int64_t T = T0; T < T1; ++T) {
+        const BInst& bi = tab[cur.x];
+        const int n1 = bi.n1, n2 = bi.n2, p1 = bi.p1;
+        const float* cf1 = bi.coef1;
+        const float* cf2 = bi.coef2;
+        uint8_t* const wt = bi.w0;
+        const uint32_t wpp = (uint32_t)bi.w_part_pitch;
+        const float g0 = bi.g0, g1 = bi.g1, g2 = bi.g2, g3 = bi.g3;
+        const int a1 = cur.y, a2 = cur.z;
+        const int i1 = a1 + 2 * cp;
+        const bool in1 = i1 < n1;               // n1 even: both columns, or neither
+        float4 ctr[2];                          // this thread's values, split: (hi, lo) x 2
+        if (FUSE) {
+            const double tau = bi.tau;
+            double* D = from ? bi.U : bi.S;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i2 = a2 + r0 + 16 * q;
+                double2 v = ui[q];
+                if (in1 && i2 < n2) {
+                    v.x = fma(tau, mx::f2d(yi[FUSE ? q : 0].x), v.x);
+                    v.y = fma(tau, mx::f2d(yi[FUSE ? q : 0].y), v.y);
+                    bad |= !mx::finite_bits(v.x) || !mx::finite_bits(v.y);
+                    *(double2*)(D + (i1 + n1 * i2)) = v;
+                }
+                mx::d2ff(v.x, ctr[q].x, ctr[q].y);
+                mx::d2ff(v.y, ctr[q].z, ctr[q].w);
+                *(float4*)&sp[r0 + 16 * q + 1][j0] = ctr[q];
+            }
+            if (ring) {
+                double v = ur;
+                const int j1 = a1 + rc, j2 = a2 + rr;
+                if ((unsigned)j1 < (unsigned)n1 && (unsigned)j2 < (unsigned)n2) v = fma(tau, mx::f2d(yr), v);
+                float2 h;
+                mx::d2ff(v, h.x, h.y);
+                sp[rr + 1][rc + 2] = h;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                mx::d2ff(ui[q].x, ctr[q].x, ctr[q].y);
+                mx::d2ff(ui[q].y, ctr[q].z, ctr[q].w);
+                *(float4*)&sp[r0 + 16 * q + 1][j0] = ctr[q];
+            }
+            if (ring) {
+                float2 h;
+                mx::d2ff(ur, h.x, h.y);
+                sp[rr + 1][rc + 2] = h;
+            }
+        }
+        if (T + 1 < T1) {                // the next tile's loads overlap this tile's stencil
+            cur = __ldg(tiles + T + 1);
+            fetch(cur);
+        }
+        float c1a[2], c1c[2], c1s[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            c1a[j] = in1 ? __ldg(cf1 + i1 + j) : 0.f;
+            c1c[j] = in1 ? __ldg(cf1 + n1 + i1 + j) : 0.f;
+            c1s[j] = in1 ? __ldg(cf1 + 2 * n1 + i1 + j) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = r0 + 16 * q;
+            const int i2 = a2 + r;
+            if (!in1 || i2 >= n2) continue;
+            const float2 lft = sp[r + 1][j0 - 1], rgt = sp[r + 1][j0 + 2];
+            const float4 up = *(const float4*)&sp[r][j0];
+            const float4 dn = *(const float4*)&sp[r + 2][j0];
+            const float2 cc[2] = {make_float2(ctr[q].x, ctr[q].y), make_float2(ctr[q].z, ctr[q].w)};
+            const float2 nbl[2] = {lft, cc[0]}, nbr[2] = {cc[1], rgt};
+            const float2 nbu[2] = {make_float2(up.x, up.y), make_float2(up.z, up.w)};
+            const float2 nbd[2] = {make_float2(dn.x, dn.y), make_float2(dn.z, dn.w)};
+            const float c2s = __ldg(cf2 + 2 * n2 + i2), c2a = __ldg(cf2 + i2), c2c = __ldg(cf2 + n2 + i2);
+            float out[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float uh = cc[j].x, ul = cc[j].y;
+                const float u = uh + ul;
+                // g is autonomous in a batch: 0 or a cubic (zero coefficients for g = 0)
+                float acc = fmaf(fmaf(fmaf(g3, u, g2), u, g1), u, g0);
+                // the edge coefficients are exactly zero and the halo holds zeros there
+                acc = fmaf(c1s[j], u, acc);
+                acc = fmaf(c1a[j], (nbl[j].x - uh) + (nbl[j].y - ul), acc);
+                acc = fmaf(c1c[j], (nbr[j].x - uh) + (nbr[j].y - ul), acc);
+                acc = fmaf(c2s, u, acc);
+                acc = fmaf(c2a, (nbu[j].x - uh) + (nbu[j].y - ul), acc);
+                acc = fmaf(c2c, (nbd[j].x - uh) + (nbd[j].y - ul), acc);
+                out[j] = acc;
+            }
+            uint32_t v0[3], v1[3];
+            split_parts<F>(out[0], 0.f, v0);
+            split_parts<F>(out[1], 0.f, v1);
+            const uint32_t pos = (uint32_t)(i1 + p1 * i2);          // even: n1, p1 even
+            if (F::kElem == 2) {
+                uint32_t* wp = (uint32_t*)((uint16_t*)wt + pos);
+                wp[0] = v0[0] | (v1[0] << 16);
+                wp[wpp >> 1] = v0[1] | (v1[1] << 16);
+                if (F::kAParts == 3) wp[wpp] = v0[2] | (v1[2] << 16);
+            } else {
+                uint2* wp = (uint2*)((uint32_t*)wt + pos);
+                wp[0] = make_uint2(v0[0], v1[0]);
+                wp[wpp >> 1] = make_uint2(v0[1], v1[1]);
+                if (F::kAParts == 3) wp[wpp] = make_uint2(v0[2], v1[2]);
+            }
+        }
+        __syncthreads();
+    }
+    if (FUSE && bad) atomicOr(status, MM_STATUS_NONFINITE);
+}
+
 // U = u + tau y (one DFMA per element) from the state buffer `from` (0: U itself,
 // 1: S), non-finite results flagged.
 __global__ void __launch_bounds__(256) batch_update_kernel(const BInst* __restrict__ tab,
@@ -247,6 +409,7 @@ struct mm_batch_s {
     int4* chunks = nullptr;                 // update pass: {instance, start, length}
     int64_t nchunks = 0;
     int4* ptiles = nullptr;                 // prepass: {instance, a_1, a_2} of every 32 x 32 tile
+    bool paired = false;                    // every n1 even, every state 16-byte aligned
     int64_t ntiles = 0;
     unsigned int* status = nullptr;
     int use_graph = 1;
@@ -300,7 +463,11 @@ int tucker_modes(mm_batch_s* b, cudaStream_t s) {
 int64_t ew_grid(const mm_batch_s* b) { return std::min<int64_t>(b->nchunks, (int64_t)num_sms() * 8); }
 
 typedef void (*PrepassKernel)(const BInst*, const int4*, int64_t, int, unsigned int*);
-PrepassKernel prepass_kernel_of(int prec, bool fuse) {
+PrepassKernel prepass_kernel_of(int prec, bool fuse, bool paired) {
+    if (paired)
+        return prec == MM_BF16X3
+                   ? (fuse ? batch_prepass2_kernel<FormBF16, true> : batch_prepass2_kernel<FormBF16, false>)
+                   : (fuse ? batch_prepass2_kernel<FormTF32, true> : batch_prepass2_kernel<FormTF32, false>);
     return prec == MM_BF16X3 ? (fuse ? batch_prepass_kernel<FormBF16, true> : batch_prepass_kernel<FormBF16, false>)
                              : (fuse ? batch_prepass_kernel<FormTF32, true> : batch_prepass_kernel<FormTF32, false>);
 }
@@ -310,7 +477,7 @@ PrepassKernel prepass_kernel_of(int prec, bool fuse) {
 int prepass(mm_batch_s* b, bool fuse, int from, cudaStream_t s) {
     const int64_t grid = std::min<int64_t>(b->ntiles, (int64_t)num_sms() * 8);
     TraceScope tr(KC_PREPASS, s);
-    auto k = prepass_kernel_of(b->prec, fuse);
+    auto k = prepass_kernel_of(b->prec, fuse, b->paired);
     k<<<(unsigned)grid, 256, 0, s>>>(b->tab, b->ptiles, b->ntiles, from, b->status);
     MM_LAUNCH_CHECK();
     return MM_OK;
@@ -510,6 +677,8 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
     cudaStream_t s = (cudaStream_t)stream;
     mm_batch_s* b = new mm_batch_s();
     b->count = count; b->prec = prec; b->scheme = scheme;
+    b->paired = true;
+    for (int j = 0; j < count; ++j) b->paired = b->paired && n1[j] % 2 == 0 && !((uintptr_t)U[j] & 15);
     b->use_graph = tune ? tune->graph : 1;
     int rc = MM_OK;
     std::vector<int> cls_of;
@@ -562,6 +731,7 @@ extern "C" int expint_batch_create(mm_batch* out, int count, const mm_plan* plan
         }
         TcClassSpec& m1 = b->spec1[c];
         m1.X = matrix_view(prec, C.W, (int64_t)cnt * C.n2, C.n1);
+        if (m1.X.part_pitch * 3 >= (int64_t(1) << 31)) b->paired = false;   // 32-bit part offsets
         m1.rows = C.n2;
         m1.M = matrix_view(prec, C.phi1, (int64_t)cnt * C.n1, C.n1);
         m1.ncols = C.n1;

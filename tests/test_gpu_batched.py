@@ -112,6 +112,26 @@ def test_batch_runs_split_anywhere_agree_bitwise(api, form, graph):
             np.testing.assert_array_equal(a, u.cpu().numpy(), err_msg=f"{p.name} {split}")
 
 
+def test_batch_paired_and_single_column_prepass_agree_bitwise(api, form):
+    """A batch whose instances all have an even n_1 runs the two-columns-per-thread
+    prepass; one odd-sized instance switches the whole batch to the one-column kernel.
+    Both must give the same states for the shared instances, bit for bit (over a run, so
+    the fused update-and-prepass pass is compared too), and the odd instance must match
+    the oracle."""
+    even = small_batch(steps=4)
+    rng = np.random.default_rng(8)
+    A1, A2 = wl.fd_matrix(45, 0.03), wl.fd_matrix(38, 0.03)
+    odd = wl.Problem(name="ac_odd", A=[A1, A2], u0=rng.uniform(-0.9, 0.9, (38, 45)),
+                     g_kind=wl.G_CUBIC, cubic=(0.0, 1.0, 0.0, -1.0), tau=1e-3, steps=4,
+                     scheme=wl.EXPEULER)
+    got_even, _ = run_batch(api, even, form, 4, autotune=False, nc_cap=128)
+    got_mixed, _ = run_batch(api, even + [odd], form, 4, autotune=False, nc_cap=128)
+    for a, b, p in zip(got_even, got_mixed, even):
+        np.testing.assert_array_equal(a, b, err_msg=p.name)
+    ref = integrate(OracleProblem.from_problem(odd, lmax=1), odd.u0, odd.scheme, odd.steps)
+    assert rel_err_inf(got_mixed[-1], ref) <= TOL_STEP
+
+
 def test_batch_autotune_picks_a_candidate(api, form):
     """The autotuner's schedule: a candidate width per size class, kept per class only
     when faster than the best uniform width; the tuned batch still reproduces the
