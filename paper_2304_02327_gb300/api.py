@@ -376,11 +376,39 @@ def batch_tile_plan(n1: Sequence[int], n2: Sequence[int], prec: str = "bf16x3", 
     return np.frombuffer(buf, dtype=np.int32).reshape(-1, 4).copy()
 
 
-def setup_batch(problems: Sequence["wl.Problem"], prec: str = "bf16x3"):
-    """Plans, nonlinearities and device states of a list of independent problems."""
+def flat_offsets(problems: Sequence["wl.Problem"]):
+    """Offsets (in doubles) of the states packed one after the other, each starting on a
+    16-byte boundary, and the total length."""
+    offs, o = [], 0
+    for p in problems:
+        offs.append(o)
+        o += (p.u0.size + 1) // 2 * 2
+    return offs, o
+
+
+def setup_batch(problems: Sequence["wl.Problem"], prec: str = "bf16x3", flat: bool = False):
+    """Plans, nonlinearities and device states of a list of independent problems.  With
+    flat=True the states are views of one device buffer (packed by flat_offsets, so one
+    copy moves them all), returned as a fourth value."""
     plans, gs, Us = [], [], []
     for p in problems:
         plans.append(Plan(p.A, p.tau, ell_for_scheme(p.scheme), prec))
         gs.append(Nonlinearity.from_problem(p))
-        Us.append(torch.from_numpy(np.ascontiguousarray(p.u0)).cuda())
-    return plans, gs, Us
+    if not flat:
+        Us = [torch.from_numpy(np.ascontiguousarray(p.u0)).cuda() for p in problems]
+        return plans, gs, Us
+    Us, buf = flat_states(problems)
+    return plans, gs, Us, buf
+
+
+def flat_states(problems: Sequence["wl.Problem"]):
+    """The problems' initial states as views of one device buffer (flat_offsets), and
+    the buffer."""
+    offs, total = flat_offsets(problems)
+    buf = torch.zeros(total, dtype=torch.float64, device="cuda")
+    Us = []
+    for p, o in zip(problems, offs):
+        u = buf[o:o + p.u0.size].view(p.u0.shape)
+        u.copy_(torch.from_numpy(np.ascontiguousarray(p.u0)))
+        Us.append(u)
+    return Us, buf

@@ -1,4 +1,4 @@
-"""The bench's reference arm and byte model, on the host (no GPU).
+"""The bench's reference arm, byte model and packed batch layout, on the host (no GPU).
 
 The reference arm times the FP64 oracle itself and must print one JSON line with the
 fields of the bench contract; the algorithmic bytes of a contraction launch follow
@@ -8,6 +8,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -44,3 +45,18 @@ def test_contraction_byte_model():
     phi4 = 3 * 4 * 320 * 320
     expect4 = (4 * (8 * N + phi4 + 8 * N) + 2 * (8 * N + phi4 + 4 * N)) / 6
     assert bench.mixed_bytes_per_launch(p, "tf32x3") == pytest.approx(expect4)
+
+
+def test_flat_offsets_pack_states_on_16_byte_boundaries():
+    """The packed state layout of a batch: each state starts on a 16-byte boundary
+    (an even number of doubles), states do not overlap, the total covers them all."""
+    from paper_2304_02327_gb300 import api, workloads as wl
+    probs = wl.batched_allen_cahn(count=7, seed=3, steps=1, sizes=(48, 64, 96))
+    rng = np.random.default_rng(1)
+    A1, A2 = wl.fd_matrix(5, 0.02), wl.fd_matrix(3, 0.02)
+    probs.append(wl.Problem(name="odd", A=[A1, A2], u0=rng.uniform(-1, 1, (3, 5)), tau=1e-3))
+    offs, total = api.flat_offsets(probs)
+    assert all(o % 2 == 0 for o in offs)
+    ends = [o + p.u0.size for o, p in zip(offs, probs)]
+    assert all(e <= o2 for e, o2 in zip(ends, offs[1:]))
+    assert ends[-1] <= total and total - ends[-1] <= 1
