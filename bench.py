@@ -65,7 +65,6 @@ OTHER_CONFIGS = ("ac2d_n64_expeuler", "adr3d_n128_etd2rk", "riccati_n2048_expeul
 ORACLE_WHOLE_RUN = ("ac2d_n64_expeuler", "adr3d_n128_etd2rk")
 L2_FLUSH_BYTES = 512 << 20          # > 126 MB L2, written between timed steps
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 4 FP64 flop/clk x 2.07 GHz
-CUBLAS_DGEMM_TFLOPS_MEASURED = 1.10          # torch.matmul float64 8192^3 on this pool
 TF32_NOMINAL_RATIO = 1.1 / 2.25                # nominal dense TF32 / BF16 tensor rate
 NPROD = {"tf32x3": 4, "bf16x3": 6}             # MMA products per split contraction
 ELEM = {"tf32x3": 4, "bf16x3": 2}              # bytes of one operand part element
@@ -204,6 +203,36 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def library_gemm_tflops():
+    """Context for the roofline denominators, measured live: cuBLAS GEMM throughput
+    through torch.matmul in FP64 (4096^3), TF32 and BF16 (8192^3), median of 5 each.
+    (The FP64 peak used as denominator stays the unit-count derivation and the TF32 one
+    the measured BF16 peak x the nominal ratio.)"""
+    import torch
+    out = {}
+    for name, n, dt, tf32 in (("fp64", 4096, torch.float64, False), ("tf32", 8192, torch.float32, True),
+                              ("bf16", 8192, torch.bfloat16, False)):
+        old = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=torch.float32).to(dt)
+        b = torch.randn(n, n, device="cuda", dtype=torch.float32).to(dt)
+        torch.matmul(a, b)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        torch.backends.cuda.matmul.allow_tf32 = old
+        out[name] = 2.0 * n ** 3 / (float(np.median(ts)) / 1e3) / 1e12
+        del a, b
+    torch.cuda.empty_cache()
+    out["note"] = "torch.matmul (cuBLAS), FP64 4096^3, TF32 and BF16 8192^3, median of 5, TFLOP/s"
+    return out
 
 
 def hbm_peak():
@@ -414,7 +443,7 @@ def roofline_single(p, prec, launches, ksteps, ms_step):
                 "flops_per_launch": flops_per_launch,
                 "timing": f"eager traced run of {ksteps} steps (the timed steps replay a CUDA graph)",
                 "peak_note": "FP64 peak derived: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 "
-                             f"TFLOP/s); cuBLAS DGEMM measured {CUBLAS_DGEMM_TFLOPS_MEASURED} TFLOP/s"}
+                             "TFLOP/s); cuBLAS DGEMM measured live: library_gemm_tflops"}
     n_launch, k_ms = launches[api.KC_CONTRACT_TF32]
     avg = k_ms / n_launch if n_launch else None
     peak, note = tensor_peak(prec)
@@ -940,6 +969,7 @@ def ours(args):
         "launches_by_kernel": head["launches_by_kernel"],
         "graph": head["graph"],
         "clocks": head["clocks"],
+        "library_gemm_tflops": library_gemm_tflops(),
     }
     if mixed:
         line["mixed"] = mixed
