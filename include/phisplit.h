@@ -297,18 +297,28 @@ typedef struct mm_batch_s* mm_batch;
  *          own tau is used for its instance.  The plans must outlive the batch.
  *   g      host array of count descriptors (MM_G_NONE or MM_G_CUBIC), or NULL.
  *   U      host array of count device pointers, n1 x n2 doubles each (i_1
- *          fastest), 8-byte aligned; the batch updates them in place.
+ *          fastest), 8-byte aligned; the batch updates them in place.  When
+ *          every n1 is even and every U 16-byte aligned the prepass takes two
+ *          columns per thread (same results, fewer instructions).
  *   scheme MM_EXPEULER (others: MM_ERR_UNSUPPORTED).
- * Allocates the batch's device memory (packed operands: about 2 (parts) x 2 +
- * 4 bytes of FP32 result per element, plus each instance's phi_1 parts), copies
- * the instances' phi_1 parts, builds the tile lists (and autotunes), then
- * synchronises `stream`.  Errors: MM_ERR_ARG, MM_ERR_UNSUPPORTED, MM_ERR_SHAPE,
+ * Allocates the batch's device memory (packed operands: about 2 x 3 (parts) x 2 +
+ * 4 bytes of FP32 result per element, each instance's phi_1 parts, and a second
+ * FP64 state of every instance, 8 bytes per element, for the fused passes of
+ * expint_batch_run), copies the instances' phi_1 parts, builds the tile lists
+ * (and autotunes), then synchronises `stream`.  Errors: MM_ERR_ARG,
+ * MM_ERR_UNSUPPORTED, MM_ERR_SHAPE (an instance with 2^31 elements or more),
  * MM_ERR_NOMEM, MM_ERR_CUDA; *out is NULL on error.
  */
 MM_API int expint_batch_create(mm_batch* out, int count, const mm_plan* plans, const mm_nonlin* g,
                                double* const* U, int scheme, const mm_tune* tune, void* stream);
 
-/* nsteps steps of every instance, stream-ordered, no synchronisation.  With the
+/* nsteps steps of every instance (Section 3.2, eq. (19)), stream-ordered, no
+ * synchronisation.  Within a run the update u + tau y of one step and the prepass
+ * K u + g of the next are one pass: it reads the state from one buffer and writes
+ * the updated state to the other (the caller's U, the batch's second set, the
+ * caller's U, ...), so that neighbouring tiles never see each other's new values;
+ * the last step's update writes the caller's U.  Every value is bit for bit what
+ * separate passes produce, so a run of k steps equals k runs of one step.  With the
  * graph option the first run with a given nsteps captures the steps (on a stream
  * of the batch) and every run replays the graph on `stream`.  t0 is the time of
  * the first step (the supported g are autonomous).  Errors: MM_ERR_ARG,
