@@ -301,8 +301,9 @@ typedef struct mm_batch_s* mm_batch;
  *          every n1 is even and every U 16-byte aligned the prepass takes two
  *          columns per thread (same results, fewer instructions).
  *   scheme MM_EXPEULER (others: MM_ERR_UNSUPPORTED).
- * Allocates the batch's device memory (packed operands: about 2 x 3 (parts) x 2 +
- * 4 bytes of FP32 result per element, each instance's phi_1 parts, and a second
+ * Allocates the batch's device memory (packed operands: the two directions' split
+ * inputs, 6 bytes per element each for BF16x3, 8 for TF32x3, and 4 bytes of FP32
+ * result per element; each instance's phi_1 parts; and a second
  * FP64 state of every instance, 8 bytes per element, for the fused passes of
  * expint_batch_run), copies the instances' phi_1 parts, builds the tile lists
  * (and autotunes), then synchronises `stream`.  Errors: MM_ERR_ARG,
