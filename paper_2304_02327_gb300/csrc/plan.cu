@@ -7,8 +7,8 @@
 // which needs all phi_j, j <= l, at every squaring and so yields them all.
 // The paper evaluates the scaled functions by Gauss-Lobatto quadrature of
 // eq. (4a); here the scaled phi_L (L = ell_max) is the truncated Taylor series
-// of eq. (4b) in Horner form, and phi_{l-1}(Y) = Y phi_l(Y) + I/(l-1)! gives
-// the lower ones.  With ||Y||_1 <= 1 and 18 Taylor terms the truncation is below
+// of eq. (4b), evaluated by Paterson-Stockmeyer blocks of four (Horner for L = 0),
+// and phi_{l-1}(Y) = Y phi_l(Y) + I/(l-1)! gives the lower ones.  With ||Y||_1 <= 1 and 18 Taylor terms the truncation is below
 // 1/19! ~ 8e-18 relative to ||phi_L||, so every phi_l(Y) is exact to rounding
 // (the terms Y^i/(i+L)! never exceed 1/L!, so the alternating sum of a
 // dissipative Y cancels little).  Scaling to 1 rather than lower keeps the
@@ -35,6 +35,15 @@ __global__ void scale_copy_kernel(const double* __restrict__ src, double* __rest
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = a * src[i];
+}
+
+// dst = w1 D1 + w2 D2 + diag I (n x n)
+__global__ void lincomb_kernel(double* __restrict__ dst, const double* __restrict__ D1, double w1,
+                               const double* __restrict__ D2, double w2, double diag, int n) {
+    int64_t count = (int64_t)n * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = w1 * D1[i] + w2 * D2[i] + ((i % n == i / n) ? diag : 0.0);
 }
 
 __global__ void fill_identity_kernel(double* dst, int n, double v) {
@@ -157,14 +166,39 @@ int form_phis(int n, const double* A, double tau, int L, double* const* out, dou
         // Y = tau A / 2^s
         scale_copy_kernel<<<grid_for(nn), 256, 0, s>>>(A, Y, ldexp(tau, -sq), nn);
         MM_LAUNCH_CHECK();
-        // Horner: phi_L(Y) = sum_{i=0}^{T} Y^i/(i+L)!, P <- Y P + I/(i+L)!
+        // phi_L(Y) = sum_{i=0}^{T} c_i Y^i, c_i = 1/(i+L)!
         double* P = out[L];
-        fill_identity_kernel<<<grid_for(nn), 256, 0, s>>>(P, n, 1.0 / fact(kTaylorTerms + L));
-        MM_LAUNCH_CHECK();
-        for (int i = kTaylorTerms - 1; i >= 0; --i) {
-            rc = square_gemm(n, Y, P, H, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 1.0 / fact(i + L), s);
+        if (L == 0) {
+            // Horner: P <- Y P + c_i I
+            fill_identity_kernel<<<grid_for(nn), 256, 0, s>>>(P, n, 1.0 / fact(kTaylorTerms + L));
+            MM_LAUNCH_CHECK();
+            for (int i = kTaylorTerms - 1; i >= 0; --i) {
+                rc = square_gemm(n, Y, P, H, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 1.0 / fact(i + L), s);
+                if (rc) goto done;
+                double* t = P; P = H; H = t;
+            }
+        } else {
+            // Paterson-Stockmeyer in blocks of four (7 products instead of 18): with
+            // B_j = sum_{k<4} c_{4j+k} Y^k, phi_L = B_0 + Y^4 (B_1 + Y^4 (B_2 + Y^4 (B_3 + Y^4 B_4))),
+            // each step one product whose epilogue adds B_j.  Y^2, Y^3, Y^4 live in buffers
+            // free until the lower phi are formed (tmp[0], tmp[1], and tmp[2] or out[0]).
+            static_assert(kTaylorTerms == 18, "the blocks below cover c_0 .. c_18");
+            double* Y2 = tmp[0];
+            double* Y3 = tmp[1];
+            double* Y4 = L >= 2 ? tmp[2] : out[0];
+            auto c = [&](int i) { return i <= kTaylorTerms ? 1.0 / fact(i + L) : 0.0; };
+            rc = square_gemm(n, Y, Y, Y2, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0.0, s);
+            if (!rc) rc = square_gemm(n, Y, Y2, Y3, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0.0, s);
+            if (!rc) rc = square_gemm(n, Y2, Y2, Y4, 1.0, nullptr, 0, nullptr, 0, nullptr, 0, 0.0, s);
             if (rc) goto done;
-            double* t = P; P = H; H = t;
+            lincomb_kernel<<<grid_for(nn), 256, 0, s>>>(P, Y, c(17), Y2, c(18), c(16), n);   // B_4
+            MM_LAUNCH_CHECK();
+            for (int j = 3; j >= 0; --j) {
+                rc = square_gemm(n, Y4, P, H, 1.0, Y, c(4 * j + 1), Y2, c(4 * j + 2), Y3, c(4 * j + 3),
+                                 c(4 * j), s);
+                if (rc) goto done;
+                double* t = P; P = H; H = t;
+            }
         }
         if (P != out[L]) {
             MM_CUDA_TRY(cudaMemcpyAsync(out[L], P, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
