@@ -185,3 +185,23 @@ def test_batch_full_config_sampled_instances(api):
         p = probs[k]
         ref = integrate(OracleProblem.from_problem(p, lmax=1), p.u0, p.scheme, p.steps)
         assert rel_err_inf(got[k], ref) <= TOL_STEP, (k, p.n[0])
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+def test_batch_nonfinite_state_raises_status(api, steps):
+    """A NaN planted (on the host) in one instance's initial state reaches the batch's
+    status word, through the closing update pass (one step) and through the fused
+    update-and-prepass passes of a longer run; the other instances are unaffected."""
+    probs = small_batch(steps=steps)
+    probs[3].u0[5, 7] = np.nan
+    plans, gs, Us = api.setup_batch(probs, "bf16x3")
+    b = api.Batch(plans, gs, Us, autotune=False, nc_cap=128)
+    b.run(steps)
+    torch.cuda.synchronize()
+    assert b.status(reset=True) & api.STATUS_NONFINITE
+    assert b.status() == 0
+    ref_probs = small_batch(steps=steps)
+    got, _ = run_batch(api, ref_probs, "bf16x3", steps, autotune=False, nc_cap=128)
+    for k, (u, g) in enumerate(zip(Us, got)):
+        if k != 3:
+            np.testing.assert_array_equal(u.cpu().numpy(), g)

@@ -279,3 +279,16 @@ def test_mixed_thin_3d_grids(api, form, sizes):
     p = wl.adr_3d(seed=9, steps=3, scheme=wl.ETD2RK, sizes=sizes)
     got, ref = run_pair(api, p, form)
     assert rel_err_inf(got, ref) <= TOL_STEP and rel_err_fro(got, ref) <= TOL_STEP
+
+
+@pytest.mark.parametrize("scheme", [wl.EXPEULER, wl.ETD2RK])
+def test_mixed_nonfinite_state_raises_status(api, form, scheme):
+    """A NaN planted on the host in the initial state reaches the plan's status word
+    through the split-precision update passes."""
+    p = wl.adr_3d(seed=5, steps=2, scheme=scheme, sizes=(40, 33, 24))
+    p.u0[3, 4, 5] = np.nan
+    plan, g, U = api.setup(p, form)
+    api.expint_step(plan, p.scheme, U, 2, g=g)
+    torch.cuda.synchronize()
+    assert plan.status(reset=True) & api.STATUS_NONFINITE
+    assert plan.status() == 0
