@@ -55,6 +55,7 @@ from paper_2304_02327_gb300 import parallel, workloads as wl  # noqa: E402
 
 METRIC = "DOF-steps/s"
 L2_BYTES = 129 * 10**6        # GB300 L2 (a state above it is not L2-resident between steps)
+E2E_BUFS = 3                  # e2e pipeline depth: a buffer's copy in, step, copy out in flight
 DEFAULT_WORKLOAD = "adr3d_n320_etd2rk"
 DEFAULT_BATCH = "batch_ac2d_1024_expeuler"
 # The other measured configurations, recorded beside the headline in every form:
@@ -377,16 +378,16 @@ def time_single(api, p, prec, args, flush, stream, world, local, do_e2e=True):
     if do_e2e:
         # ---- e2e: per step, a state in from pinned host memory, one step through the C
         # ABI, the result out to pinned host memory.  Successive steps take independent
-        # states (a stream of problems), double-buffered: step k's copy in and step
+        # states (a stream of problems), E2E_BUFS buffers deep: step k's copy in and step
         # k - 1's copy out run on their own streams beside step k's kernels, which stay
         # in order on one stream (they share the plan's workspace) ----
         U_host = torch.from_numpy(np.ascontiguousarray(p.u0)).pin_memory()
-        outs = [torch.empty_like(U_host).pin_memory() for _ in range(2)]
-        bufs = [torch.empty_like(U) for _ in range(2)]
+        outs = [torch.empty_like(U_host).pin_memory() for _ in range(E2E_BUFS)]
+        bufs = [torch.empty_like(U) for _ in range(E2E_BUFS)]
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-        ev_in = [torch.cuda.Event() for _ in range(2)]
-        ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(E2E_BUFS)]
+        ev_done = [torch.cuda.Event() for _ in range(E2E_BUFS)]
+        ev_out = [torch.cuda.Event() for _ in range(E2E_BUFS)]
         for bq in bufs:                      # each buffer's step graph, captured untimed
             bq.copy_(U_host)
             api.expint_step(plan, p.scheme, bq, 1, g=g, ws=ws)
@@ -399,9 +400,9 @@ def time_single(api, p, prec, args, flush, stream, world, local, do_e2e=True):
         s_in.wait_stream(stream)
         s_out.wait_stream(stream)
         for k in range(e2e_steps):
-            b = k % 2
+            b = k % E2E_BUFS
             with torch.cuda.stream(s_in):
-                if k >= 2:
+                if k >= E2E_BUFS:
                     s_in.wait_event(ev_out[b])       # buffer b's previous result is out
                 bufs[b].copy_(U_host, non_blocking=True)
                 ev_in[b].record(s_in)
@@ -419,7 +420,7 @@ def time_single(api, p, prec, args, flush, stream, world, local, do_e2e=True):
         rec["e2e"] = {"value": parallel.job_throughput([N * e2e_steps] * world, e2e_ms / 1e3),
                       "unit": METRIC, "steps": e2e_steps,
                       "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
-                      "pipeline": "independent states, two device buffers: copies in and out "
+                      "pipeline": f"independent states, {E2E_BUFS} device buffers: copies in and out "
                                   "overlap the kernels of neighbouring steps"}
     del plan, g, U, ws
     torch.cuda.empty_cache()
@@ -654,26 +655,26 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
     b.set_graph(True)
 
     # ---- e2e: every state in from pinned host memory, one step, every state out.  The
-    # states sit packed in one device buffer (one copy each way per step); two batches
-    # over two such buffers take the steps in turn, so that one batch's copies overlap
+    # states sit packed in one device buffer (one copy each way per step); E2E_BUFS batches
+    # over as many such buffers take the steps in turn, so that one batch's copies overlap
     # the other's kernels (successive steps take independent states; the kernels stay in
     # order on one stream) ----
     offs, total = api.flat_offsets(probs)
     host_in = torch.zeros(total, dtype=torch.float64).pin_memory()
     for p, o in zip(probs, offs):
         host_in[o:o + p.u0.size].copy_(torch.from_numpy(np.ascontiguousarray(p.u0)).reshape(-1))
-    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(2)]
+    host_out = [torch.empty_like(host_in).pin_memory() for _ in range(E2E_BUFS)]
     pipes = []
-    for _ in range(2):
+    for _ in range(E2E_BUFS):
         Ue, fbuf = api.flat_states(probs)
         be = api.Batch(plans, gs, Ue, autotune=False, nc_cap=b.info()["nc_cap"], graph=True)
         be.run(1)                            # its one-step graph, captured untimed
         pipes.append((be, fbuf))
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
-    e2e_steps = min(args.steps, 6)
+    ev_in = [torch.cuda.Event() for _ in range(E2E_BUFS)]
+    ev_done = [torch.cuda.Event() for _ in range(E2E_BUFS)]
+    ev_out = [torch.cuda.Event() for _ in range(E2E_BUFS)]
+    e2e_steps = min(args.steps, 9)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
@@ -682,10 +683,10 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
     s_in.wait_stream(stream)
     s_out.wait_stream(stream)
     for k in range(e2e_steps):
-        j = k % 2
+        j = k % E2E_BUFS
         be, fbuf = pipes[j]
         with torch.cuda.stream(s_in):
-            if k >= 2:
+            if k >= E2E_BUFS:
                 s_in.wait_event(ev_out[j])           # this buffer's previous result is out
             fbuf.copy_(host_in, non_blocking=True)
             ev_in[j].record(s_in)
@@ -788,8 +789,8 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
            "speedup_vs_fp64_loop": fp_ms / ms_step,
            "e2e": {"value": e2e_value, "unit": METRIC, "steps": e2e_steps,
                    "h2d_bytes_per_step": dof * 8, "d2h_bytes_per_step": dof * 8,
-                   "pipeline": "all states packed in one buffer, one copy each way per step; two "
-                               "batches alternate so that copies overlap the other batch's kernels"},
+                   "pipeline": f"all states packed in one buffer, one copy each way per step; {E2E_BUFS} "
+                               "batches take the steps in turn so that copies overlap the others' kernels"},
            "gpu_launches": sum(counts.values()),
            "launches_by_kernel": {"contract_tf32": counts[api.KC_CONTRACT_TF32],
                                   "prepass": counts[api.KC_PREPASS], "update": counts[api.KC_SPLIT]},
