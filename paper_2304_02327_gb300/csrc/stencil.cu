@@ -292,8 +292,9 @@ __global__ void __launch_bounds__(256, 4) stencil3d_kernel(StencilArgsMixed a, i
     }
 }
 
-// The 3D K u + g prepass with the fewest instructions per element (no Riccati or
-// dense terms: d = 3 has neither; N < 2^31, so 32-bit offsets).  The same
+// The 3D K u + g prepass fed from registers, taken when the state admits no TMA map
+// (odd n_1; the TMA-fed march below is the usual one).  No Riccati or dense terms
+// (d = 3 has neither); N < 2^31, so 32-bit offsets.  The same
 // arithmetic as stencil3d_kernel: g, the row sums times u and the six differences
 // of the double-float split, in FP32, then the form's split of the result.  It
 // marches a 32 x 32 tile of (i_1, i_2) along i_3 with two shared-memory planes:
