@@ -762,7 +762,9 @@ def time_batched(api, name, prec, args, flush, stream, world, local, rank, do_ch
                "widths_by_class": sched["widths"], "per_class_widths_kept": sched["per_class"],
                "tucker_ms_uniform_width": sched["tucker_ms_uniform"],
                "tucker_ms_chosen": sched["tucker_ms_chosen"],
-               "tile_order": "decreasing cost, taken round-robin by one CTA per SM"},
+               "tile_order": "decreasing cost, one CTA per SM taking tiles "
+                             + ("round-robin" if sched["tile_order"] == "round-robin"
+                                else "round-robin with every other round reversed")},
            "tiles_per_mode": info["tiles_mode1"],
            "plan_ms": plan_ms, "batch_create_ms": create_ms,
            "graph": "the K timed steps are one run: one CUDA graph launch, each step's update "

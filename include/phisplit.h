@@ -343,6 +343,11 @@ MM_API int expint_batch_info(mm_batch b, int* nclasses, int* nc_cap, int64_t* ti
 MM_API int expint_batch_schedule(mm_batch b, int32_t* nc_per_class, int max_classes, int* nclasses,
                                  float* ms_uniform, float* ms_chosen);
 
+/* Host query: the tile order the grouped launches use: 0 = decreasing cost, taken
+ * round-robin by the CTAs; 1 = the same with every other round of tiles reversed (the
+ * autotuner keeps it when it times faster).  Errors: MM_ERR_ARG. */
+MM_API int expint_batch_tile_order(mm_batch b);
+
 /* Host setting: expint_batch_run replays a captured graph (on != 0, the default of
  * mm_tune) or launches the kernels directly (on = 0: each launch then carries its
  * own trace events, see mm_trace_enable).  Errors: MM_ERR_ARG. */

@@ -37,6 +37,7 @@ EXPORTS = ("phi_plan_create", "phi_plan_destroy", "phi_plan_info", "phi_plan_get
            "mm_trace_enable", "mm_trace_read", "tucker_apply_noalloc",
            "expint_batch_create", "expint_batch_run", "expint_batch_status", "expint_batch_info",
            "expint_batch_destroy", "expint_batched", "mm_batch_tile_plan", "expint_batch_schedule",
+           "expint_batch_tile_order",
            "expint_batch_set_graph")
 KC_CONTRACT_FP64, KC_CONTRACT_TF32, KC_PREPASS, KC_SPLIT = 0, 1, 2, 3
 
@@ -97,6 +98,7 @@ def lib():
     L.expint_batch_info.argtypes = [vp, P(i32), P(i32), P(i64), P(i64)]
     L.expint_batch_destroy.argtypes = [vp]
     L.expint_batch_schedule.argtypes = [vp, P(ctypes.c_int32), i32, P(i32), P(ctypes.c_float), P(ctypes.c_float)]
+    L.expint_batch_tile_order.argtypes = [vp]
     L.expint_batch_set_graph.argtypes = [vp, i32]
     L.expint_batched.argtypes = [i32, P(vp), P(Nonlin), P(vp), i32, f64, i32, P(Tune), vp]
     L.mm_batch_tile_plan.argtypes = [i32, P(i64), P(i64), i32, i32, i32, P(ctypes.c_int32), i64, P(i64)]
@@ -333,15 +335,17 @@ class Batch:
         return {"classes": nc.value, "nc_cap": cap.value, "tiles_mode1": t.value, "dof": dof.value}
 
     def schedule(self) -> dict:
-        """The autotuner's outcome: per-class tile widths and the Tucker time of a
-        step with the best uniform width and with the widths in use."""
+        """The autotuner's outcome: per-class tile widths, the Tucker time of a step
+        with the best uniform width and with the schedule in use, and the tile order."""
         n = self.info()["classes"]
         w = (ctypes.c_int32 * max(n, 1))()
         nc, mu, mc = ctypes.c_int(), ctypes.c_float(), ctypes.c_float()
         per = _check(lib().expint_batch_schedule(self.handle, w, n, ctypes.byref(nc), ctypes.byref(mu),
                                                  ctypes.byref(mc)), "expint_batch_schedule")
+        order = _check(lib().expint_batch_tile_order(self.handle), "expint_batch_tile_order")
         return {"per_class": bool(per), "widths": list(w)[:n], "tucker_ms_uniform": mu.value,
-                "tucker_ms_chosen": mc.value}
+                "tucker_ms_chosen": mc.value,
+                "tile_order": "alternate rounds reversed" if order == 1 else "round-robin"}
 
     def set_graph(self, on: bool) -> None:
         """Replay captured graphs (default) or launch the kernels directly."""

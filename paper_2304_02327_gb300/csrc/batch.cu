@@ -397,6 +397,7 @@ struct mm_batch_s {
     float tune_ms_uniform = 0.f;             // autotuner: best uniform width's Tucker time
     float tune_ms_chosen = 0.f;              //   and the time of the widths kept
     int tune_per_class = 0;                  //   1: the per-class widths won
+    int tile_order = 0;                      //   0 round-robin, 1 alternate rounds reversed
     struct Launch {                          // groups of <= MM_TC_MAX_CLASSES classes
         int c0, nc;
         int4* tiles1 = nullptr;
@@ -432,12 +433,24 @@ struct mm_batch_s {
 
 namespace {
 
+// Tile order of a grouped launch: the list comes sorted by decreasing cost and the
+// C = min(tiles, SMs) CTAs take it round-robin (CTA j: tiles j, j + C, ...).  Order 1
+// reverses every other round of C tiles, so that the CTA given the dearest tile of one
+// round gets the cheapest of the next (the autotuner keeps it if it is faster).
+void order_tiles(std::vector<int4>& t, int order) {
+    if (order != 1) return;
+    const size_t C = (size_t)std::min<int64_t>((int64_t)t.size(), num_sms());
+    for (size_t w = C; w < t.size(); w += 2 * C) std::reverse(t.begin() + w, t.begin() + std::min(t.size(), w + C));
+}
+
 int build_tiles(mm_batch_s* b, cudaStream_t s) {
     for (auto& L : b->launches) {
         std::vector<int4> t1, t2;
         int rc = tc_group_tiles(b->prec, &b->spec1[L.c0], L.nc, &b->nc_cap[L.c0], t1);
         if (!rc) rc = tc_group_tiles(b->prec, &b->spec2[L.c0], L.nc, &b->nc_cap[L.c0], t2);
         if (rc) return rc;
+        order_tiles(t1, b->tile_order);
+        order_tiles(t2, b->tile_order);
         if (!L.tiles1 || (int64_t)t1.size() > L.cap1 || (int64_t)t2.size() > L.cap2) return MM_ERR_ARG;
         L.n1 = (int64_t)t1.size();
         L.n2 = (int64_t)t2.size();
@@ -552,7 +565,9 @@ int time_class(mm_batch_s* b, int c, int nc, cudaStream_t s, cudaEvent_t e0, cud
 //   1. every candidate width for all classes at once; the fastest is the uniform choice;
 //   2. each class alone at every candidate width (a size class's best width depends
 //      on its n: how its columns split into tiles and how many tiles it brings);
-//   3. the per-class choices together, kept only if faster than the uniform one.
+//   3. the per-class choices together, kept only if faster than the uniform one;
+//   4. the chosen widths with every other round of tiles reversed (order_tiles), kept
+//      only if faster.
 // Tiles within a launch are always ordered by decreasing cost (the CTAs take them
 // round-robin).  The times of both schedules are kept for expint_batch_schedule.
 int autotune(mm_batch_s* b, cudaStream_t s) {
@@ -586,14 +601,23 @@ int autotune(mm_batch_s* b, cudaStream_t s) {
         b->nc_cap = per;
         if (!(rc = build_tiles(b, s))) rc = time_ms(all_modes, s, e0, e1, &per_ms);
     }
+    if (!rc) {
+        b->tune_ms_uniform = best_ms;
+        b->tune_per_class = per_ms < best_ms;
+        b->tune_ms_chosen = b->tune_per_class ? per_ms : best_ms;
+        if (!b->tune_per_class)
+            for (auto& v : b->nc_cap) v = best;
+        // 4. the tile order of the chosen widths: alternate rounds reversed, kept if faster
+        b->tile_order = 1;
+        float ord_ms = 0.f;
+        if (!(rc = build_tiles(b, s)) && !(rc = time_ms(all_modes, s, e0, e1, &ord_ms))) {
+            if (ord_ms < b->tune_ms_chosen) b->tune_ms_chosen = ord_ms;
+            else b->tile_order = 0;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    b->tune_ms_uniform = best_ms;
-    b->tune_per_class = per_ms < best_ms;
-    b->tune_ms_chosen = b->tune_per_class ? per_ms : best_ms;
-    if (!b->tune_per_class)
-        for (auto& v : b->nc_cap) v = best;
     return build_tiles(b, s);
 }
 
@@ -931,6 +955,11 @@ extern "C" int expint_batch_schedule(mm_batch b, int32_t* nc_per_class, int max_
     if (ms_uniform) *ms_uniform = b->tune_ms_uniform;
     if (ms_chosen) *ms_chosen = b->tune_ms_chosen;
     return b->tune_per_class;
+}
+
+extern "C" int expint_batch_tile_order(mm_batch b) {
+    if (!b) return MM_ERR_ARG;
+    return b->tile_order;
 }
 
 extern "C" int expint_batch_set_graph(mm_batch b, int on) {

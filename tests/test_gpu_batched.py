@@ -144,6 +144,7 @@ def test_batch_autotune_picks_a_candidate(api, form):
     assert set(sch["widths"]) <= {160, 128, 96, 64}
     assert sch["per_class"] or len(set(sch["widths"])) == 1
     assert 0 < sch["tucker_ms_chosen"] <= sch["tucker_ms_uniform"]
+    assert sch["tile_order"] in ("round-robin", "alternate rounds reversed")
     for p, g in zip(probs, got):
         plan, gg, U = api.setup(p, form)
         api.expint_step(plan, p.scheme, U, 3, g=gg)
